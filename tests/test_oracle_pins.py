@@ -1,0 +1,326 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form (singular value soft-thresholding, the full-observation optimum), a
+brute-force or dense evaluation, central finite differences, an invariant
+(Lemma "equivalent"), a published generator output, or the subgradient
+optimality condition of (MC).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import bm_oracle as O
+from synth import planted_uniform, random_factors
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dense(ix):
+    M = np.zeros((ix.m, ix.n))
+    mask = np.zeros((ix.m, ix.n), dtype=bool)
+    ri = ix.rows_of_entries()
+    M[ri, ix.col] = ix.val
+    mask[ri, ix.col] = True
+    return M, mask
+
+
+def _small_problem(m=40, n=60, frac=0.3, rank=3, seed=11, lam=0.5):
+    p = planted_uniform(m=m, n=n, rank=rank, frac=frac, noise_sd=0.1, lam=lam, seed=seed)
+    return p, O.build_index(p.m, p.n, p.rows, p.cols, p.vals)
+
+
+# ---------------------------------------------------------------- index build
+def test_index_matches_dense_mask_bruteforce():
+    rng = np.random.default_rng(0)
+    for (m, n) in [(7, 9), (9, 7), (1, 5), (5, 1), (13, 13)]:
+        flat = rng.choice(m * n, size=max(1, (m * n) // 3), replace=False)
+        rows, cols = flat // n, flat % n
+        vals = rng.standard_normal(flat.shape[0])
+        ix = O.build_index(m, n, rows, cols, vals)
+        D = np.full((m, n), np.nan)
+        D[rows, cols] = vals
+        if ix.transposed:
+            D = D.T
+        assert ix.m <= ix.n and ix.transposed == (m > n)
+        # CSR: walk the dense matrix row by row, left to right
+        k = 0
+        for i in range(ix.m):
+            js = np.nonzero(~np.isnan(D[i]))[0]
+            assert ix.row_ptr[i] == k
+            assert np.array_equal(ix.col[k:k + js.size], js)
+            assert np.array_equal(ix.val[k:k + js.size], D[i, js])
+            k += js.size
+        assert ix.row_ptr[-1] == k
+        # CSC: column by column, top to bottom
+        q = 0
+        for j in range(ix.n):
+            is_ = np.nonzero(~np.isnan(D[:, j]))[0]
+            assert ix.col_ptr[j] == q
+            assert np.array_equal(ix.row[q:q + is_.size], is_)
+            assert np.array_equal(ix.cval[q:q + is_.size], D[is_, j])
+            q += is_.size
+        # permutations are mutually inverse and map equal entries
+        ri = ix.rows_of_entries()
+        assert np.array_equal(ix.row[ix.csr2csc], ri)
+        assert np.array_equal(ix.csc2csr[ix.csr2csc], np.arange(ix.nnz))
+
+
+def test_index_rejects_bad_input():
+    with pytest.raises(ValueError):
+        O.build_index(3, 3, [0, 0], [1, 1], [1.0, 2.0])          # duplicate pair
+    with pytest.raises(ValueError):
+        O.build_index(3, 3, [0, 3], [1, 1], [1.0, 2.0])          # row out of range
+    with pytest.raises(ValueError):
+        O.build_index(3, 3, [0, 1], [1, -1], [1.0, 2.0])         # negative column
+    with pytest.raises(ValueError):
+        O.build_index(3, 3, [0, 1], [1, 1], [1.0, np.nan])       # non-finite value
+    ix = O.build_index(4, 6, [], [], [])                           # empty Omega is valid
+    assert ix.nnz == 0 and np.all(ix.row_ptr == 0)
+
+
+# ---------------------------------------------------------------- loss, gradient
+def test_loss_matches_dense_and_finite_differences():
+    p, ix = _small_problem()
+    W, H = random_factors(ix.m, ix.n, 5, seed=3, scale=0.5)
+    W = W.astype(np.float64)
+    H = H.astype(np.float64)
+    lam = 0.7
+    f, F, gW, gH, r = O.loss_grad(ix, W, H, lam)
+    M, mask = _dense(ix)
+    Rd = (W @ H.T - M) * mask
+    assert math.isclose(f, 0.5 * np.sum(Rd ** 2), rel_tol=1e-13)
+    assert math.isclose(F, f + 0.5 * lam * (np.sum(W ** 2) + np.sum(H ** 2)), rel_tol=1e-13)
+    # central differences of F~ in 40 random coordinates
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for _ in range(20):
+        i, c = rng.integers(ix.m), rng.integers(5)
+        Wp, Wm = W.copy(), W.copy()
+        Wp[i, c] += h
+        Wm[i, c] -= h
+        fd = (O.objective(ix, Wp, H, lam) - O.objective(ix, Wm, H, lam)) / (2 * h)
+        assert abs(fd - gW[i, c]) <= 1e-7 * max(1.0, abs(gW[i, c]))
+        j = rng.integers(ix.n)
+        Hp, Hm = H.copy(), H.copy()
+        Hp[j, c] += h
+        Hm[j, c] -= h
+        fd = (O.objective(ix, W, Hp, lam) - O.objective(ix, W, Hm, lam)) / (2 * h)
+        assert abs(fd - gH[j, c]) <= 1e-7 * max(1.0, abs(gH[j, c]))
+
+
+# ---------------------------------------------------------------- orth, LmSVD
+def test_orth_spans_and_drops():
+    rng = np.random.default_rng(2)
+    F = np.linalg.qr(rng.standard_normal((30, 4)))[0]
+    M = np.hstack([rng.standard_normal((30, 3)), F[:, :2] @ rng.standard_normal((2, 2))])
+    M = np.hstack([M, M[:, :1] * 3.0])            # a duplicate direction
+    Q2, _ = O.orth(M, F=F, tau=1e-10)
+    assert Q2.shape[1] == 3                        # 2 in ran(F), 1 duplicate dropped
+    B = np.hstack([F, Q2])
+    assert np.allclose(B.T @ B, np.eye(7), atol=1e-12)
+    P = B @ B.T
+    assert np.allclose(P @ M, M, atol=1e-10)       # ran(M) inside ran([F, Q2])
+
+
+def test_lmsvd_finds_leading_eigenvectors():
+    rng = np.random.default_rng(4)
+    m, n, k = 50, 80, 6
+    U, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    s = np.geomspace(10.0, 0.01, m)
+    Z = (U * s) @ V.T
+    for p in (0, 1, 2):
+        Uh, theta, it, nL = O.lmsvd(lambda X: Z @ (Z.T @ X), rng.standard_normal((m, k)), p=p,
+                                    tol=1e-15, imax=400, tau=1e-14)
+        assert np.allclose(theta, s[:k] ** 2, rtol=1e-10)
+        assert np.allclose(np.abs(Uh.T @ U[:, :k]), np.eye(k), atol=1e-7)
+
+
+# ---------------------------------------------------------------- prox step
+def _state_from(W, H, opt):
+    U0, _ = O.orth(W, tau=1e-14)
+    return O.State(W=W, H=H, U_prev=U0, U_prev2=None, u=None, psi=opt.psi0,
+                   rank_hist=[W.shape[1], W.shape[1]], prev_warm_cols=W.shape[1] + 1, t=0,
+                   bm_changed=True)
+
+
+def _full_problem(m=12, n=20, seed=5):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n))
+    rows, cols = np.divmod(np.arange(m * n), n)
+    return A, O.build_index(m, n, rows, cols, A[rows, cols])
+
+
+def test_prox_full_observation_is_svt_closed_form():
+    """With Omega = all entries and alpha = 1, Z = A for any X, so one PG step
+    gives prox_{lam||.||_*}(A) = U diag([s - lam]_+) V^T (Eq. "proxnuc")."""
+    A, ix = _full_problem()
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    lam = 0.5 * (s[3] + s[4])                       # rank 4 after thresholding
+    X_star = (U[:, :4] * (s[:4] - lam)) @ Vt[:4]
+    opt = O.Options(alpha=1.0, lmsvd_tol=1e-15, lmsvd_imax=500, tau=1e-14, ritz_rel=1e-12)
+    W, H = random_factors(ix.m, ix.n, 6, seed=9)
+    st = _state_from(W.astype(np.float64), H.astype(np.float64), opt)
+    st2, info = O.prox_step(ix, st, lam, k_max=10, opt=opt)
+    assert info.k_new == 4
+    assert np.allclose(st2.W @ st2.H.T, X_star, atol=1e-10)
+    assert np.allclose(info.sigma, s[:4] - lam, rtol=1e-11)
+
+
+def test_prox_factors_are_balanced_and_eps_formula():
+    """Lemma "equivalent": after the refactor W^T W = H^T H = diag(Sigma);
+    eps_t = ||Z - U^ U^^T Z||_F equals the dense evaluation."""
+    p, ix = _small_problem()
+    W, H = random_factors(ix.m, ix.n, 5, seed=3, scale=0.5)
+    W = W.astype(np.float64)
+    H = H.astype(np.float64)
+    opt = O.Options(lmsvd_imax=6, lmsvd_tol=0.0, tau=1e-12)
+    st = _state_from(W, H, opt)
+    st2, info = O.prox_step(ix, st, p.lam, k_max=20, opt=opt)
+    D = np.diag(info.sigma)
+    assert np.allclose(st2.W.T @ st2.W, D, atol=1e-10)
+    assert np.allclose(st2.H.T @ st2.H, D, atol=1e-10)
+    # dense epsilon: Z~ = U^ U^^T Z with U^ spanned by the prox output plus truncated part
+    M, mask = _dense(ix)
+    Z = W @ H.T - opt.alpha * (W @ H.T - M) * mask
+    sh = info.sigma_hat
+    assert math.isclose(info.eps ** 2 + np.sum(sh ** 2), np.sum(Z ** 2), rel_tol=1e-10)
+
+
+def test_prox_descent_condition_back():
+    """Eq. "back" with L = 1, alpha = 1.99 and delta = 0.9999 (alpha < 2 delta / L)."""
+    p, ix = _small_problem()
+    W, H = random_factors(ix.m, ix.n, 5, seed=3, scale=0.5)
+    W = W.astype(np.float64)
+    H = H.astype(np.float64)
+    opt = O.Options()
+    st2, _ = O.prox_step(ix, _state_from(W, H, opt), p.lam, 20, opt)
+    M, mask = _dense(ix)
+    f = lambda X: 0.5 * np.sum(((X - M) * mask) ** 2)
+    Xt = W @ H.T
+    Xn = st2.W @ st2.H.T
+    g = (Xt - M) * mask
+    assert f(Xn) <= f(Xt) + np.sum(g * (Xn - Xt)) + 0.9999 / 1.99 * np.sum((Xn - Xt) ** 2) + 1e-12
+
+
+def test_init_step_exact_on_low_rank_full_observation():
+    """Sec. "Initialization": with A of rank 3 fully observed and k_{-1} = 6,
+    the HMT sketch captures ran(A A^T), Nystrom is exact, and the initial PG
+    step from X_{-1} = 0 with alpha = 1 equals SVT_lam(A)."""
+    rng = np.random.default_rng(8)
+    m, n = 15, 25
+    A = rng.standard_normal((m, 3)) @ rng.standard_normal((3, n))
+    rows, cols = np.divmod(np.arange(m * n), n)
+    ix = O.build_index(m, n, rows, cols, A[rows, cols])
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    lam = 0.3 * s[2]
+    X_star = (U[:, :3] * (s[:3] - lam)) @ Vt[:3]
+    st, info = O.init_step(ix, lam, 6, 10, O.Options(tau=1e-14, ritz_rel=1e-9))
+    assert info.k_new == 3
+    assert np.allclose(st.W @ st.H.T, X_star, atol=1e-9)
+
+
+# ---------------------------------------------------------------- BM phase
+def test_quartic_argmin_bruteforce():
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        c = rng.standard_normal(5)
+        c[4] = abs(c[4]) + 1e-3
+        s = O.quartic_argmin(c)
+        grid = np.linspace(0, 20, 400001)
+        phi = np.polyval(c[::-1], grid)
+        assert np.polyval(c[::-1], s) <= phi.min() + 1e-9 * (1 + abs(phi.min()))
+        assert s >= 0
+
+
+def test_line_search_coefficients_match_objective():
+    p, ix = _small_problem()
+    W, H = random_factors(ix.m, ix.n, 4, seed=3, scale=0.5)
+    DW, DH = random_factors(ix.m, ix.n, 4, seed=4, scale=0.2)
+    W, H, DW, DH = (x.astype(np.float64) for x in (W, H, DW, DH))
+    lam = 0.3
+    r = O.residual(ix, W, H)
+    c = O.line_search_coeffs(ix, W, H, DW, DH, r, lam)
+    for s in (0.0, 0.3, -1.2, 2.5):
+        ref = O.objective(ix, W + s * DW, H + s * DH, lam)
+        assert math.isclose(np.polyval(c[::-1], s), ref, rel_tol=1e-12)
+
+
+def test_bm_phase_nonincreasing():
+    p, ix = _small_problem()
+    W, H = random_factors(ix.m, ix.n, 5, seed=3, scale=0.5)
+    st = _state_from(W.astype(np.float64), H.astype(np.float64), O.Options())
+    st2, trace = O.bm_phase(ix, st, p.lam, 25)
+    trace.append(O.objective(ix, st2.W, st2.H, p.lam))
+    assert all(b <= a * (1 + 1e-15) for a, b in zip(trace, trace[1:]))
+
+
+# ---------------------------------------------------------------- Algorithm 1
+def test_solve_full_observation_reaches_closed_form_optimum():
+    A, ix = _full_problem(10, 16, seed=12)
+    s = np.linalg.svd(A, compute_uv=False)
+    lam = 0.5 * (s[2] + s[3])
+    F_star = np.sum(np.where(s > lam, lam * s - 0.5 * lam ** 2, 0.5 * s ** 2))
+    st, info = O.solve(ix, lam, 4, 8, O.Options(), max_outer=60, tol=1e-15)
+    assert abs(info.F_hist[-1] - F_star) <= 1e-10 * F_star
+    assert st.W.shape[1] == 3
+
+
+def test_solve_matches_dense_soft_impute_and_optimality():
+    """Tiny planted problem: the objective equals the dense FP64 proximal-gradient
+    optimum, the rank is identified (Thm "identify"), and the subgradient
+    optimality condition of (MC) holds at the returned X = U diag(Sigma) V^T."""
+    p, ix = _small_problem(m=40, n=60, frac=0.35, rank=3, seed=21, lam=1.0)
+    M, mask = _dense(ix)
+    X = np.zeros_like(M)
+    for _ in range(20000):
+        U, s, Vt = np.linalg.svd(X - 1.0 * (X - M) * mask, full_matrices=False)
+        Xn = (U * np.maximum(s - p.lam, 0)) @ Vt
+        done = np.linalg.norm(Xn - X) <= 1e-14 * max(1.0, np.linalg.norm(X))
+        X = Xn
+        if done:
+            break
+    sX = np.linalg.svd(X, compute_uv=False)
+    rank_star = int(np.sum(sX > 1e-8))
+    F_star = 0.5 * np.sum(((X - M) * mask) ** 2) + p.lam * sX.sum()
+    st, info = O.solve(ix, p.lam, 4, 30, O.Options(), max_outer=400, tol=1e-15)
+    assert abs(info.F_hist[-1] - F_star) <= 1e-8 * F_star
+    assert st.W.shape[1] == rank_star
+    # optimality: G = P_Omega(X - A); U^T G V = -lam I; off-blocks vanish; ||(I-UU^T)G(I-VV^T)||_2 <= lam
+    Xs = st.W @ st.H.T
+    U, s, Vt = np.linalg.svd(Xs, full_matrices=False)
+    U, V = U[:, :rank_star], Vt[:rank_star].T
+    G = (Xs - M) * mask
+    tau = 1e-6
+    assert np.linalg.norm(U.T @ G @ V + p.lam * np.eye(rank_star)) <= tau * (1 + p.lam)
+    PU = np.eye(ix.m) - U @ U.T
+    PV = np.eye(ix.n) - V @ V.T
+    assert np.linalg.norm(PU @ G @ V) <= tau * (1 + p.lam)
+    assert np.linalg.norm(U.T @ G @ PV) <= tau * (1 + p.lam)
+    assert np.linalg.norm(PU @ G @ PV, 2) <= p.lam * (1 + tau)
+
+
+def test_objective_monotone_over_cycles_with_alpha_one():
+    """With alpha = 1 <= 1/L, Eq. "decrease" holds and F(X_t) is nonincreasing."""
+    p, ix = _small_problem(seed=31)
+    st, info = O.solve(ix, p.lam, 4, 30, O.Options(alpha=1.0), max_outer=30, tol=0.0)
+    F = info.F_hist
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(F, F[1:]))
+
+
+# ---------------------------------------------------------------- generator
+def test_counter_generator_matches_published_splitmix64():
+    lines = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64.txt")) if not l.startswith("#")]
+    for idx, hexv in lines:
+        state = (int(idx) * O._GAMMA) % (1 << 64)
+        assert int(O._mix64(np.array([state], dtype=np.uint64))[0]) == int(hexv, 16)
+    x = O.counter_normal(0, 7, 200000)
+    assert abs(x.mean()) < 0.01 and abs(x.std() - 1.0) < 0.01
+    # Kolmogorov-Smirnov distance against the normal CDF
+    xs = np.sort(x)
+    cdf = 0.5 * (1 + np.vectorize(math.erf)(xs / math.sqrt(2)))
+    ks = np.max(np.abs(cdf - np.arange(1, xs.size + 1) / xs.size))
+    assert ks < 0.01
