@@ -1,0 +1,223 @@
+/*
+ * bm.h -- C ABI of the GB300 (sm_103a) implementation of the data-parallel
+ * hot path of BM-Global (Lee, Liang, Tang & Toh, arXiv 2204.14067) for
+ * nuclear-norm regularised matrix completion
+ *
+ *     min_X  F(X) = 1/2 ||P_Omega(X - A)||_F^2 + lambda ||X||_*      (Eq. "MC")
+ *
+ * solved through the factorisation X = W H^T                          (Eq. "MF")
+ *
+ *     min_{W,H}  1/2 ||P_Omega(W H^T - A)||_F^2 + lambda/2 (||W||^2 + ||H||^2)
+ *
+ * alternating BM phases with inexact proximal-gradient steps (Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *  - Orientation: callers pass an m x n matrix.  If m > n the library stores
+ *    the transpose internally (the paper assumes m <= n, Sec. 1); factors,
+ *    gradients and index dumps that are documented as "caller orientation"
+ *    are mapped back, those documented as "internal" are not.
+ *  - Indexing is 0-based; indices are int32, counts int64.
+ *  - Dense factors are row-major with leading dimension k (W[i*k + c]).
+ *  - Pointers may be host or device memory; the library detects which
+ *    (cudaPointerGetAttributes) and copies as needed.  Inputs are copied
+ *    and never retained; output buffers are owned by the caller.
+ *  - Every call returns a bm_status and never aborts or throws.  The text
+ *    of the last failure on a handle is returned by bm_last_error(h);
+ *    failures without a handle are reported by bm_last_error(NULL).
+ *  - A handle owns its device memory and a CUDA stream; handles are
+ *    independent, one handle must not be used by two threads at once.
+ */
+#ifndef BM_GB300_H
+#define BM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bm_ctx* bm_handle;
+
+typedef enum {
+  BM_OK = 0,
+  BM_ERR_INVALID = 1,       /* bad argument: sizes, indices, duplicates, non-finite values */
+  BM_ERR_OOM = 2,           /* device allocation failed */
+  BM_ERR_CUDA = 3,          /* a CUDA call failed */
+  BM_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
+  BM_ERR_NUMERIC = 5,       /* NaN/Inf in the objective or a small eigenproblem */
+  BM_ERR_NOT_CONVERGED = 6  /* bm_solve stopped on max_outer or time_limit */
+} bm_status;
+
+/* Solver parameters.  Defaults (bm_default_options) follow the paper where
+ * it gives a value and the design notes where it does not. */
+typedef struct {
+  double alpha;          /* PG step size; 1.99 (Sec. 5.1: L = 1, alpha < 2 delta / L) */
+  int32_t bm_epochs;     /* y: BM iterations per cycle; 3 (Sec. 5.1.1, x = 1, y = 3) */
+  int32_t pg_steps;      /* x: inexact PG steps per cycle; 1 */
+  int32_t lmsvd_p;       /* LmSVD memory p_t (Algorithm 2); 1 */
+  int32_t lmsvd_imax;    /* LmSVD iteration cap; 50 */
+  int32_t lmsvd_min_iter;/* Rayleigh-Ritz steps before the stop test; 2 */
+  double lmsvd_tol;      /* stop when max |theta - theta_prev| <= tol * theta_1; 1e-6 */
+  double tau;            /* orth(): drop Gram eigenvalues <= tau (Eq. "orth-W"); 1e-6 */
+  double ritz_rel;       /* Algorithm 2 J_s: keep s_j > ritz_rel * s_1; 1e-6 */
+  double psi0;           /* safeguard noise level psi_0 (Sec. "Ensuring sufficient precision"); 0.1 */
+  int32_t k_init;        /* k_{-1}: sketch size of the initial PG step (Sec. "Initialization"); 8 */
+  int32_t precision;     /* 0: FP32 factors; 1: BF16 factor copies for the gathers */
+  uint64_t seed;         /* counter-based RNG key for the sketch and xi_t */
+} bm_options;
+
+/* Result of one inexact PG step (Eq. "inexactpg", "truncate"). */
+typedef struct {
+  int32_t k_new;         /* rank of X_{t+1}: singular values surviving the threshold */
+  int32_t warm_cols;     /* columns of the LmSVD warm start U^{t,0} */
+  int32_t lmsvd_iters;   /* Rayleigh-Ritz steps taken */
+  int32_t n_L;           /* applications of L(U) = Z Z^T U */
+  int32_t cap_hit;       /* 1 if more than k_max values survived (rank capped) */
+  int32_t pad_;
+  double eps;            /* ||Z_t - Z~_t||_F (Sec. "Inexact PG step", monitoring formula) */
+  double F;              /* objective F(X_{t+1}) = f + lambda * sum(Sigma) */
+} bm_prox_info;
+
+typedef struct {
+  int32_t max_outer;     /* cycles of Algorithm 1; default 100 */
+  int32_t pad_;
+  double tol;            /* stop when |F_t - F_{t-1}| / (1 + |F_{t-1}|) < tol; default 1e-10 */
+  double F_target;       /* stop when F <= F_target (<= 0: unused) */
+  double time_limit_s;   /* wall-clock limit (<= 0: none) */
+} bm_solve_opts;
+
+typedef struct {
+  int32_t outer;         /* cycles run */
+  int32_t k;             /* final rank */
+  int32_t converged;     /* 1 if tol or F_target was met */
+  int32_t pad_;
+  double F;              /* final objective */
+  double seconds;        /* wall time of the solve */
+} bm_solve_info;
+
+/* Fill *o with the defaults listed in bm_options.  Never fails for o != NULL. */
+bm_status bm_default_options(bm_options* o);
+
+/*
+ * bm_create -- upload Omega and A, build the index structures.
+ * Paper: Omega is an index set and P_Omega the sampling operator (Sec. 1,
+ * Eq. "MC"); the m <= n convention (Sec. 1).
+ *   m, n        caller's matrix size, both >= 1.
+ *   nnz         |Omega| >= 0 (< 2^31).
+ *   rows, cols  int32[nnz], 0 <= rows < m, 0 <= cols < n, no repeated pair.
+ *   vals        float32[nnz] observed values A_ij, finite.
+ *   lambda      nuclear-norm weight, > 0.
+ *   k_max       rank cap, 1 <= k_max <= min(m, n).
+ *   opt         solver options (NULL: defaults).
+ *   out         receives the handle.
+ * Builds, on the device, CSR sorted by (row, col) and CSC sorted by (col, row)
+ * of the internal orientation (bit-exact canonical order).  Factors start at
+ * k = 0 (X = 0).  Errors: BM_ERR_INVALID for bad sizes, out-of-range or
+ * repeated indices, non-finite values; BM_ERR_OOM; BM_ERR_CUDA.
+ */
+bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                    const float* vals, double lambda, int32_t k_max, const bm_options* opt,
+                    bm_handle* out);
+
+/* Free all device memory of h (NULL is ignored). */
+void bm_destroy(bm_handle h);
+
+/* Text of the last failure on h (or of the last failure without a handle if
+ * h is NULL).  The pointer stays valid until the next call on h. */
+const char* bm_last_error(bm_handle h);
+
+/* Run the handle's work on `stream` (a cudaStream_t; NULL restores the
+ * handle's own stream).  The stream must outlive its use by h. */
+bm_status bm_set_stream(bm_handle h, void* stream);
+
+/* Sizes: internal m <= n, nnz, whether the caller's matrix was transposed,
+ * current rank k.  Any output pointer may be NULL. */
+bm_status bm_dims(bm_handle h, int64_t* m, int64_t* n, int64_t* nnz, int32_t* transposed,
+                  int32_t* k);
+
+/*
+ * bm_get_index -- copy the index structures (internal orientation) into
+ * caller buffers (host or device; any may be NULL):
+ *   row_ptr int64[m+1], col int32[nnz], val float[nnz]        CSR by (row, col)
+ *   col_ptr int64[n+1], row int32[nnz], cval float[nnz]       CSC by (col, row)
+ *   csr2csc int64[nnz]  CSC position of each CSR entry
+ */
+bm_status bm_get_index(bm_handle h, int64_t* row_ptr, int32_t* col, float* val, int64_t* col_ptr,
+                       int32_t* row, float* cval, int64_t* csr2csc);
+
+/*
+ * bm_set_factors -- set X = W H^T (caller orientation): W float[m*k],
+ * H float[n*k], row-major, 0 <= k <= k_max.  Resets the safeguard state of
+ * the PG steps (the next bm_prox_step warm-starts from orth(W)).
+ */
+bm_status bm_set_factors(bm_handle h, int32_t k, const float* W, const float* H);
+
+/* bm_get_factors -- copy the current factors (caller orientation) into
+ * W float[m*k], H float[n*k] (either may be NULL); *k receives the rank. */
+bm_status bm_get_factors(bm_handle h, int32_t* k, float* W, float* H);
+
+/*
+ * bm_loss_grad -- the sparse loss and gradient of (MF)/(BM-nuclear) at the
+ * current factors (Eq. "mf"):
+ *   f  = 1/2 sum_{(i,j) in Omega} (<W_i, H_j> - A_ij)^2
+ *   F  = f + lambda/2 (||W||_F^2 + ||H||_F^2)
+ *   gW = R H + lambda W,  gH = R^T W + lambda H,  R = P_Omega(W H^T - A)
+ * f, F: host doubles (either may be NULL).  gW float[m*k], gH float[n*k]
+ * in caller orientation, host or device, may be NULL.  FP32 arithmetic with
+ * FP64 reduction of f.  Errors: BM_ERR_NUMERIC if f is not finite.
+ */
+bm_status bm_loss_grad(bm_handle h, double* f, double* F, float* gW, float* gH);
+
+/*
+ * bm_bm_phase -- `epochs` iterations of the BM-phase solver: nonlinear
+ * conjugate gradient (Polak-Ribiere+) on (MF) with an exact line search on
+ * the quartic phi(s) = F~(W + s D_W, H + s D_H).  Each iteration keeps the
+ * non-increase condition (Eq. "nonincrease").  *F (nullable) receives the
+ * objective after the last iteration.
+ */
+bm_status bm_bm_phase(bm_handle h, int32_t epochs, double* F);
+
+/*
+ * bm_init -- the initial point: one inexact PG step from X_{-1} = 0 with
+ * alpha = 1/L = 1, using the HMT range finder on k_init Gaussian columns and
+ * the Nystrom approximation (Sec. "Initialization", Eq. "nys"), then
+ * Eq. "exactSVD", "approxSVD", "truncate".  info may be NULL.
+ */
+bm_status bm_init(bm_handle h, bm_prox_info* info);
+
+/*
+ * bm_prox_step -- one inexact PG step from X~ = W H^T (Eq. "inexactpg"):
+ * Z = X~ - alpha R; LmSVD (Algorithm 2) on L(U) = Z Z^T U warm-started from
+ * orth([U_t, W]) plus the safeguard column (Eq. "rt0", "rt"); exact SVD of
+ * U^T Z (Eq. "exactSVD"); soft-threshold by lambda*alpha (Eq. "truncate");
+ * W <- U sqrt(Sigma), H <- V sqrt(Sigma) (Algorithm 1).  alpha <= 0 uses
+ * the handle's option.  info may be NULL.
+ */
+bm_status bm_prox_step(bm_handle h, double alpha, bm_prox_info* info);
+
+/*
+ * bm_solve -- Algorithm 1: bm_init if k = 0, then cycles of bm_epochs BM
+ * iterations and pg_steps PG steps until a stopping rule of *o holds
+ * (o NULL: defaults).  info may be NULL.  Returns BM_ERR_NOT_CONVERGED if
+ * max_outer or time_limit_s ended the solve.
+ */
+bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info);
+
+/*
+ * Kernel timing for measurement.  While enabled, the library records a pair
+ * of CUDA events on the handle's stream around every launch of its kernels
+ * (no extra synchronisation).  bm_profile_read synchronises, then reports per
+ * kernel name: launches and total device milliseconds since the last enable.
+ *   names     char[cap * 48], NUL-terminated names (may be NULL)
+ *   launches  int64[cap], total_ms double[cap] (may be NULL)
+ *   count     receives the number of kernel names (<= cap written)
+ */
+bm_status bm_profile_enable(bm_handle h, int32_t enable);
+bm_status bm_profile_read(bm_handle h, int32_t cap, char* names, int64_t* launches, double* total_ms,
+                          int32_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BM_GB300_H */

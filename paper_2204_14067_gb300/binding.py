@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libbm.so (include/bm.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+functions carry the C names; arrays may be numpy arrays (host) or torch
+tensors (host or CUDA).  A failing status raises BMError with the library's
+message.  If libbm.so is missing the import of a function fails loudly; there
+is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "bm.h")
+
+BM_OK, BM_ERR_INVALID, BM_ERR_OOM, BM_ERR_CUDA, BM_ERR_TIMEOUT, BM_ERR_NUMERIC, BM_ERR_NOT_CONVERGED = range(7)
+STATUS_NAMES = ["BM_OK", "BM_ERR_INVALID", "BM_ERR_OOM", "BM_ERR_CUDA", "BM_ERR_TIMEOUT",
+                "BM_ERR_NUMERIC", "BM_ERR_NOT_CONVERGED"]
+
+
+class BMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class bm_options(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("bm_epochs", ctypes.c_int32), ("pg_steps", ctypes.c_int32),
+                ("lmsvd_p", ctypes.c_int32), ("lmsvd_imax", ctypes.c_int32), ("lmsvd_min_iter", ctypes.c_int32),
+                ("lmsvd_tol", ctypes.c_double), ("tau", ctypes.c_double), ("ritz_rel", ctypes.c_double),
+                ("psi0", ctypes.c_double), ("k_init", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class bm_prox_info(ctypes.Structure):
+    _fields_ = [("k_new", ctypes.c_int32), ("warm_cols", ctypes.c_int32), ("lmsvd_iters", ctypes.c_int32),
+                ("n_L", ctypes.c_int32), ("cap_hit", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("F", ctypes.c_double)]
+
+
+class bm_solve_opts(ctypes.Structure):
+    _fields_ = [("max_outer", ctypes.c_int32), ("pad_", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("F_target", ctypes.c_double), ("time_limit_s", ctypes.c_double)]
+
+
+class bm_solve_info(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int32), ("k", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("F", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+_lib = None
+_c = ctypes
+_P = ctypes.c_void_p
+_SIGS = {
+    "bm_default_options": (_c.c_int, [_c.POINTER(bm_options)]),
+    "bm_create": (_c.c_int, [_c.c_int64, _c.c_int64, _c.c_int64, _P, _P, _P, _c.c_double, _c.c_int32,
+                             _c.POINTER(bm_options), _c.POINTER(_P)]),
+    "bm_destroy": (None, [_P]),
+    "bm_last_error": (_c.c_char_p, [_P]),
+    "bm_set_stream": (_c.c_int, [_P, _P]),
+    "bm_dims": (_c.c_int, [_P, _P, _P, _P, _P, _P]),
+    "bm_get_index": (_c.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "bm_set_factors": (_c.c_int, [_P, _c.c_int32, _P, _P]),
+    "bm_get_factors": (_c.c_int, [_P, _P, _P, _P]),
+    "bm_loss_grad": (_c.c_int, [_P, _P, _P, _P, _P]),
+    "bm_bm_phase": (_c.c_int, [_P, _c.c_int32, _P]),
+    "bm_init": (_c.c_int, [_P, _c.POINTER(bm_prox_info)]),
+    "bm_prox_step": (_c.c_int, [_P, _c.c_double, _c.POINTER(bm_prox_info)]),
+    "bm_solve": (_c.c_int, [_P, _c.POINTER(bm_solve_opts), _c.POINTER(bm_solve_info)]),
+    "bm_profile_enable": (_c.c_int, [_P, _c.c_int32]),
+    "bm_profile_read": (_c.c_int, [_P, _c.c_int32, _P, _P, _P, _P]),
+}
+
+
+def header_symbols() -> list:
+    """Function names declared in include/bm.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bm_[a-z_0-9]+)\s*\(", txt)))
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with paper_2204_14067_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Address of a numpy array / torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _check(status: int, h=None):
+    if status != BM_OK:
+        msg = lib().bm_last_error(h)
+        raise BMError(status, msg.decode() if msg else "")
+
+
+def bm_default_options() -> bm_options:
+    o = bm_options()
+    _check(lib().bm_default_options(ctypes.byref(o)))
+    return o
+
+
+def bm_create(m, n, rows, cols, vals, lam, k_max, opt: bm_options | None = None):
+    """Returns an opaque handle (int).  rows/cols int32, vals float32."""
+    for a, dt in ((rows, "int32"), (cols, "int32"), (vals, "float32")):
+        if str(a.dtype).replace("torch.", "") != dt:
+            raise TypeError(f"expected {dt}, got {a.dtype}")
+    nnz = int(rows.shape[0])
+    h = _P()
+    st = lib().bm_create(int(m), int(n), nnz, _ptr(rows), _ptr(cols), _ptr(vals), float(lam), int(k_max),
+                         ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    _check(st, None)
+    return h.value
+
+
+def bm_destroy(h):
+    lib().bm_destroy(h)
+
+
+def bm_last_error(h=None) -> str:
+    return lib().bm_last_error(h).decode()
+
+
+def bm_set_stream(h, stream):
+    """stream: torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().bm_set_stream(h, raw), h)
+
+
+def bm_dims(h):
+    m, n, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    tr, k = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().bm_dims(h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(tr),
+                         ctypes.byref(k)), h)
+    return dict(m=m.value, n=n.value, nnz=nnz.value, transposed=bool(tr.value), k=k.value)
+
+
+def bm_get_index(h):
+    """Index arrays (internal orientation) as numpy host arrays."""
+    d = bm_dims(h)
+    m, n, nnz = d["m"], d["n"], d["nnz"]
+    out = dict(row_ptr=np.empty(m + 1, np.int64), col=np.empty(nnz, np.int32), val=np.empty(nnz, np.float32),
+               col_ptr=np.empty(n + 1, np.int64), row=np.empty(nnz, np.int32), cval=np.empty(nnz, np.float32),
+               csr2csc=np.empty(nnz, np.int64))
+    _check(lib().bm_get_index(h, *(_ptr(out[k]) for k in
+                                   ("row_ptr", "col", "val", "col_ptr", "row", "cval", "csr2csc"))), h)
+    return out
+
+
+def bm_set_factors(h, k, W, H):
+    _check(lib().bm_set_factors(h, int(k), _ptr(W), _ptr(H)), h)
+
+
+def bm_get_factors(h, m, n, W=None, H=None):
+    """Caller-orientation factors; allocates host arrays if W/H are None."""
+    kk = ctypes.c_int32()
+    _check(lib().bm_dims(h, None, None, None, None, ctypes.byref(kk)), h)
+    k = kk.value
+    if W is None:
+        W = np.zeros((m, k), np.float32)
+    if H is None:
+        H = np.zeros((n, k), np.float32)
+    _check(lib().bm_get_factors(h, ctypes.byref(kk), _ptr(W), _ptr(H)), h)
+    return W, H
+
+
+def bm_loss_grad(h, gW=None, gH=None):
+    """Returns (f, F); writes gradients into gW / gH if given."""
+    f, F = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bm_loss_grad(h, ctypes.byref(f), ctypes.byref(F), _ptr(gW), _ptr(gH)), h)
+    return f.value, F.value
+
+
+def bm_bm_phase(h, epochs):
+    F = ctypes.c_double()
+    _check(lib().bm_bm_phase(h, int(epochs), ctypes.byref(F)), h)
+    return F.value
+
+
+def _info_dict(info: bm_prox_info):
+    return {name: getattr(info, name) for name, _ in bm_prox_info._fields_ if name != "pad_"}
+
+
+def bm_init(h):
+    info = bm_prox_info()
+    _check(lib().bm_init(h, ctypes.byref(info)), h)
+    return _info_dict(info)
+
+
+def bm_prox_step(h, alpha=0.0):
+    info = bm_prox_info()
+    _check(lib().bm_prox_step(h, float(alpha), ctypes.byref(info)), h)
+    return _info_dict(info)
+
+
+def bm_solve(h, max_outer=100, tol=1e-10, F_target=0.0, time_limit_s=0.0, raise_not_converged=False):
+    o = bm_solve_opts(max_outer=int(max_outer), tol=float(tol), F_target=float(F_target),
+                      time_limit_s=float(time_limit_s))
+    info = bm_solve_info()
+    st = lib().bm_solve(h, ctypes.byref(o), ctypes.byref(info))
+    if st != BM_OK and not (st == BM_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(st, h)
+    return dict(outer=info.outer, k=info.k, converged=bool(info.converged), F=info.F, seconds=info.seconds,
+                status=st)
+
+
+def bm_profile_enable(h, enable=True):
+    _check(lib().bm_profile_enable(h, 1 if enable else 0), h)
+
+
+def bm_profile_read(h, cap=64):
+    """{kernel name: (launches, total_ms)} since the last bm_profile_enable."""
+    names = ctypes.create_string_buffer(48 * cap)
+    launches = np.zeros(cap, np.int64)
+    ms = np.zeros(cap, np.float64)
+    cnt = ctypes.c_int32()
+    _check(lib().bm_profile_read(h, cap, names, _ptr(launches), _ptr(ms), ctypes.byref(cnt)), h)
+    out = {}
+    for i in range(min(cnt.value, cap)):
+        nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out

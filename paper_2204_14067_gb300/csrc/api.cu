@@ -1,0 +1,508 @@
+// The C ABI (include/bm.h): argument checks, host/device marshalling,
+// handle lifetime, the BM phase and Algorithm 1 orchestration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "ctx.cuh"
+
+namespace bm {
+
+int num_sms() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+Profiler::~Profiler() {
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+cudaEvent_t Profiler::next() {
+  if (used == pool.size()) {
+    cudaEvent_t e;
+    BM_CUDA(cudaEventCreate(&e));
+    pool.push_back(e);
+  }
+  return pool[used++];
+}
+
+void Profiler::begin(const char* name, cudaStream_t st) {
+  cudaEvent_t a = next();
+  BM_CUDA(cudaEventRecord(a, st));
+  marks.push_back({name, {a, nullptr}});
+}
+
+void Profiler::end(cudaStream_t st) {
+  cudaEvent_t b = next();
+  BM_CUDA(cudaEventRecord(b, st));
+  marks.back().second.second = b;
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class Fn>
+bm_status guarded(bm_ctx* h, Fn&& fn) {
+  try {
+    fn();
+    return BM_OK;
+  } catch (const Error& e) {
+    (h ? h->err : g_last_error) = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    (h ? h->err : g_last_error) = "host allocation failed";
+    return BM_ERR_OOM;
+  } catch (...) {
+    (h ? h->err : g_last_error) = "unexpected exception";
+    return BM_ERR_CUDA;
+  }
+}
+
+// Copy `count` elements to a device buffer if `src` is host memory.
+template <typename T>
+const T* to_device(const T* src, int64_t count, DevBuf<T>& tmp, cudaStream_t st) {
+  if (count == 0) return src;
+  if (is_device_ptr(src)) return src;
+  tmp.alloc(count);
+  BM_CUDA(cudaMemcpyAsync(tmp.get(), src, count * sizeof(T), cudaMemcpyHostToDevice, st));
+  return tmp.get();
+}
+
+cudaMemcpyKind kind_to(const void* dst) { return is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+cudaMemcpyKind kind_from(const void* src) { return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+
+// Caller-orientation factor pointers map to internal (W, H) swapped when transposed.
+void copy_out_rows(bm_ctx& h, float* dst, const float* src, int64_t rows, int k) {
+  if (!dst || rows == 0 || k == 0) return;
+  BM_CUDA(cudaMemcpy2DAsync(dst, k * sizeof(float), src, h.ld * sizeof(float), k * sizeof(float), rows,
+                            kind_to(dst), h.stream));
+}
+
+void copy_in_rows(bm_ctx& h, float* dst, const float* src, int64_t rows, int k) {
+  BM_CUDA(cudaMemsetAsync(dst, 0, rows * h.ld * sizeof(float), h.stream));
+  if (!src || rows == 0 || k == 0) return;
+  BM_CUDA(cudaMemcpy2DAsync(dst, h.ld * sizeof(float), src, k * sizeof(float), k * sizeof(float), rows,
+                            kind_from(src), h.stream));
+}
+
+void set_rank(bm_ctx& h, int k) {
+  h.k = k;
+  h.ld = std::max(4, round_up4(k));
+}
+
+// Real roots of c1 + 2 c2 s + 3 c3 s^2 + 4 c4 s^3 = 0; pick the argmin of
+// phi(s) = c0 + c1 s + ... + c4 s^4 over s = 0 and the positive roots.
+double poly4(const double c[5], double s) { return (((c[4] * s + c[3]) * s + c[2]) * s + c[1]) * s + c[0]; }
+double dpoly4(const double c[5], double s) { return ((4 * c[4] * s + 3 * c[3]) * s + 2 * c[2]) * s + c[1]; }
+double ddpoly4(const double c[5], double s) { return (12 * c[4] * s + 6 * c[3]) * s + 2 * c[2]; }
+
+double quartic_argmin(const double c[5]) {
+  std::vector<double> roots;
+  const double a3 = 4 * c[4], a2 = 3 * c[3], a1 = 2 * c[2], a0 = c[1];
+  const double scale = std::max({std::fabs(a3), std::fabs(a2), std::fabs(a1), std::fabs(a0), 1e-300});
+  if (std::fabs(a3) > 1e-14 * scale) {
+    // s^3 + p2 s^2 + p1 s + p0 = 0, depressed with s = t - p2/3
+    const double p2 = a2 / a3, p1 = a1 / a3, p0 = a0 / a3;
+    const double q = (3 * p1 - p2 * p2) / 9.0;
+    const double r = (9 * p2 * p1 - 27 * p0 - 2 * p2 * p2 * p2) / 54.0;
+    const double disc = q * q * q + r * r;
+    if (disc > 0) {
+      const double sq = std::sqrt(disc);
+      const double s1 = std::cbrt(r + sq), s2 = std::cbrt(r - sq);
+      roots.push_back(s1 + s2 - p2 / 3.0);
+    } else {
+      const double th = std::acos(std::max(-1.0, std::min(1.0, q < 0 ? r / std::sqrt(-q * q * q) : 0.0)));
+      const double m = 2.0 * std::sqrt(std::max(0.0, -q));
+      for (int t = 0; t < 3; ++t) roots.push_back(m * std::cos((th + 2.0 * M_PI * t) / 3.0) - p2 / 3.0);
+    }
+  } else if (std::fabs(a2) > 1e-14 * scale) {
+    const double d = a1 * a1 - 4 * a2 * a0;
+    if (d >= 0) {
+      const double sq = std::sqrt(d);
+      const double qq = -0.5 * (a1 + (a1 >= 0 ? sq : -sq));
+      if (qq != 0) roots.push_back(qq / a2), roots.push_back(a0 / qq);
+      else roots.push_back(0.0);
+    }
+  } else if (std::fabs(a1) > 0) {
+    roots.push_back(-a0 / a1);
+  }
+  double best_s = 0.0, best = poly4(c, 0.0);
+  for (double s : roots) {
+    for (int it = 0; it < 3; ++it) {  // Newton polish on phi'
+      const double d2 = ddpoly4(c, s);
+      if (d2 == 0) break;
+      s -= dpoly4(c, s) / d2;
+    }
+    if (!(s > 0) || !std::isfinite(s)) continue;
+    const double v = poly4(c, s);
+    if (v < best) best = v, best_s = s;
+  }
+  return best_s;
+}
+
+double objective_now(bm_ctx& h, double* f_out = nullptr) {
+  LossOut o = loss_grad_dev(h, false, false);
+  if (f_out) *f_out = o.f;
+  return o.f + 0.5 * h.lambda * (o.nW2 + o.nH2);
+}
+
+void bm_phase_dev(bm_ctx& h, int epochs, double* F_out) {
+  const Index& ix = h.ix;
+  const int64_t mW = ix.m * h.ld, nH = ix.n * h.ld;
+  double F = 0.0;
+  double gg_prev = 0.0;
+  bool have_prev = false;
+  for (int e = 0; e < epochs; ++e) {
+    LossOut o = loss_grad_dev(h, true, true);
+    F = o.f + 0.5 * h.lambda * (o.nW2 + o.nH2);
+    BM_REQUIRE(std::isfinite(F), BM_ERR_NUMERIC, "bm_bm_phase: objective is not finite");
+    if (h.k == 0) break;
+    const double gg = dot_dev(h, h.gW.get(), h.gW.get(), mW) + dot_dev(h, h.gH.get(), h.gH.get(), nH);
+    double beta = 0.0;
+    if (have_prev && gg_prev > 0) {
+      const double gp = dot_dev(h, h.gW.get(), h.gWp.get(), mW) + dot_dev(h, h.gH.get(), h.gHp.get(), nH);
+      beta = std::max(0.0, (gg - gp) / gg_prev);
+    }
+    if (!have_prev) {
+      BM_CUDA(cudaMemsetAsync(h.DW.get(), 0, mW * sizeof(float), h.stream));
+      BM_CUDA(cudaMemsetAsync(h.DH.get(), 0, nH * sizeof(float), h.stream));
+    }
+    xpby_dev(h, h.DW.get(), h.gW.get(), (float)beta, mW);  // D = -g + beta D
+    xpby_dev(h, h.DH.get(), h.gH.get(), (float)beta, nH);
+    if (beta > 0) {
+      const double dg = dot_dev(h, h.DW.get(), h.gW.get(), mW) + dot_dev(h, h.DH.get(), h.gH.get(), nH);
+      if (dg >= 0) {
+        xpby_dev(h, h.DW.get(), h.gW.get(), 0.0f, mW);
+        xpby_dev(h, h.DH.get(), h.gH.get(), 0.0f, nH);
+      }
+    }
+    double c[5];
+    c[0] = F;
+    line_search_coeffs_dev(h, c);
+    const double s = quartic_argmin(c);
+    if (s > 0) {
+      axpy_dev(h, h.W.get(), h.DW.get(), (float)s, mW);
+      axpy_dev(h, h.H.get(), h.DH.get(), (float)s, nH);
+      h.bm_changed = true;
+      F = poly4(c, s);
+    }
+    BM_CUDA(cudaMemcpyAsync(h.gWp.get(), h.gW.get(), mW * sizeof(float), cudaMemcpyDeviceToDevice, h.stream));
+    BM_CUDA(cudaMemcpyAsync(h.gHp.get(), h.gH.get(), nH * sizeof(float), cudaMemcpyDeviceToDevice, h.stream));
+    gg_prev = gg;
+    have_prev = true;
+  }
+  if (F_out) {
+    *F_out = objective_now(h);
+  }
+  BM_CUDA(cudaStreamSynchronize(h.stream));
+}
+
+}  // namespace
+}  // namespace bm
+
+using namespace bm;
+
+extern "C" {
+
+bm_status bm_default_options(bm_options* o) {
+  if (!o) return BM_ERR_INVALID;
+  o->alpha = 1.99;
+  o->bm_epochs = 3;
+  o->pg_steps = 1;
+  o->lmsvd_p = 1;
+  o->lmsvd_imax = 50;
+  o->lmsvd_min_iter = 2;
+  o->lmsvd_tol = 1e-6;
+  o->tau = 1e-6;
+  o->ritz_rel = 1e-6;
+  o->psi0 = 0.1;
+  o->k_init = 8;
+  o->precision = 0;
+  o->seed = 0;
+  return BM_OK;
+}
+
+bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                    const float* vals, double lambda, int32_t k_max, const bm_options* opt,
+                    bm_handle* out) {
+  if (!out) {
+    g_last_error = "bm_create: out is NULL";
+    return BM_ERR_INVALID;
+  }
+  *out = nullptr;
+  bm_ctx* h = nullptr;
+  bm_status st = guarded(nullptr, [&] {
+    BM_REQUIRE(m >= 1 && n >= 1, BM_ERR_INVALID, "bm_create: m and n must be >= 1");
+    BM_REQUIRE(m < (1LL << 31) && n < (1LL << 31), BM_ERR_INVALID, "bm_create: m and n must be < 2^31");
+    BM_REQUIRE(nnz >= 0 && nnz < (1LL << 31), BM_ERR_INVALID, "bm_create: nnz must be in [0, 2^31)");
+    BM_REQUIRE(nnz == 0 || (rows && cols && vals), BM_ERR_INVALID, "bm_create: NULL index or value array");
+    BM_REQUIRE(std::isfinite(lambda) && lambda > 0, BM_ERR_INVALID, "bm_create: lambda must be finite and > 0");
+    BM_REQUIRE(k_max >= 1 && k_max <= std::min(m, n) && k_max <= 127, BM_ERR_INVALID,
+               "bm_create: k_max must be in [1, min(m, n)] and <= 127");
+    bm_options o;
+    if (opt) o = *opt; else bm_default_options(&o);
+    BM_REQUIRE(o.alpha > 0 && std::isfinite(o.alpha), BM_ERR_INVALID, "bm_create: alpha must be > 0");
+    BM_REQUIRE(o.lmsvd_p >= 0 && o.lmsvd_p <= 1, BM_ERR_INVALID, "bm_create: lmsvd_p must be 0 or 1");
+    BM_REQUIRE(o.lmsvd_imax >= 1 && o.k_init >= 1 && o.bm_epochs >= 0 && o.pg_steps >= 0, BM_ERR_INVALID,
+               "bm_create: iteration counts out of range");
+    h = new bm_ctx();
+    h->opt = o;
+    h->lambda = lambda;
+    h->k_max = k_max;
+    BM_CUDA(cudaGetDevice(&h->device));
+    BM_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
+    DevBuf<int32_t> tr, tc;
+    DevBuf<float> tv;
+    const int32_t* rd = to_device(rows, nnz, tr, h->stream);
+    const int32_t* cd = to_device(cols, nnz, tc, h->stream);
+    const float* vd = to_device(vals, nnz, tv, h->stream);
+    build_index(*h, m, n, nnz, rd, cd, vd);
+    const Index& ix = h->ix;
+    h->ldmax = round_up4(k_max + 1);
+    const int64_t mW = ix.m * h->ldmax, nH = ix.n * h->ldmax;
+    h->W.alloc(mW); h->H.alloc(nH);
+    h->gW.alloc(mW); h->gH.alloc(nH);
+    h->DW.alloc(mW); h->DH.alloc(nH);
+    h->gWp.alloc(mW); h->gHp.alloc(nH);
+    h->r_csr.alloc(std::max<int64_t>(1, nnz));
+    h->r_csc.alloc(std::max<int64_t>(1, nnz));
+    h->sc.partial.alloc(std::max<int64_t>(1, std::max(ix.rs.nslots, ix.cs.nslots)) * h->ldmax);
+    h->sc.fseg.alloc(std::max(ix.rs.nseg, ix.cs.nseg) * 4 + 4);
+    h->sc.red.alloc(4096);
+    h->sc.scal.alloc(64);
+    set_rank(*h, 0);
+    BM_CUDA(cudaMemsetAsync(h->W.get(), 0, mW * sizeof(float), h->stream));
+    BM_CUDA(cudaMemsetAsync(h->H.get(), 0, nH * sizeof(float), h->stream));
+    prox_create(*h);
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+  });
+  if (st != BM_OK) {
+    if (h) bm_destroy(h);
+    return st;
+  }
+  *out = h;
+  return BM_OK;
+}
+
+void bm_destroy(bm_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  prox_destroy(*h);
+  cudaStream_t own = h->own_stream;
+  delete h;
+  if (own) cudaStreamDestroy(own);
+}
+
+const char* bm_last_error(bm_handle h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+bm_status bm_set_stream(bm_handle h, void* stream) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+  });
+}
+
+bm_status bm_dims(bm_handle h, int64_t* m, int64_t* n, int64_t* nnz, int32_t* transposed, int32_t* k) {
+  if (!h) return BM_ERR_INVALID;
+  if (m) *m = h->ix.m;
+  if (n) *n = h->ix.n;
+  if (nnz) *nnz = h->ix.nnz;
+  if (transposed) *transposed = h->ix.transposed ? 1 : 0;
+  if (k) *k = h->k;
+  return BM_OK;
+}
+
+bm_status bm_get_index(bm_handle h, int64_t* row_ptr, int32_t* col, float* val, int64_t* col_ptr,
+                       int32_t* row, float* cval, int64_t* csr2csc) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    const Index& ix = h->ix;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+      if (dst && bytes) BM_CUDA(cudaMemcpyAsync(dst, src, bytes, kind_to(dst), h->stream));
+    };
+    cp(row_ptr, ix.row_ptr.get(), (ix.m + 1) * 8);
+    cp(col_ptr, ix.col_ptr.get(), (ix.n + 1) * 8);
+    cp(col, ix.col.get(), ix.nnz * 4);
+    cp(val, ix.val.get(), ix.nnz * 4);
+    cp(row, ix.row.get(), ix.nnz * 4);
+    cp(cval, ix.cval.get(), ix.nnz * 4);
+    cp(csr2csc, ix.csr2csc.get(), ix.nnz * 8);
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+bm_status bm_set_factors(bm_handle h, int32_t k, const float* W, const float* H) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    BM_REQUIRE(k >= 0 && k <= h->k_max, BM_ERR_INVALID, "bm_set_factors: k must be in [0, k_max]");
+    BM_REQUIRE(k == 0 || (W && H), BM_ERR_INVALID, "bm_set_factors: NULL factor");
+    set_rank(*h, k);
+    const float* Wi = h->ix.transposed ? H : W;
+    const float* Hi = h->ix.transposed ? W : H;
+    copy_in_rows(*h, h->W.get(), Wi, h->ix.m, k);
+    copy_in_rows(*h, h->H.get(), Hi, h->ix.n, k);
+    prox_reset(*h);
+    h->bm_changed = true;
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+bm_status bm_get_factors(bm_handle h, int32_t* k, float* W, float* H) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    if (k) *k = h->k;
+    float* Wo = h->ix.transposed ? H : W;
+    float* Ho = h->ix.transposed ? W : H;
+    copy_out_rows(*h, Wo, h->W.get(), h->ix.m, h->k);
+    copy_out_rows(*h, Ho, h->H.get(), h->ix.n, h->k);
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+bm_status bm_loss_grad(bm_handle h, double* f, double* F, float* gW, float* gH) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    const bool want = gW || gH;
+    LossOut o = loss_grad_dev(*h, want, false);
+    const double Fv = o.f + 0.5 * h->lambda * (o.nW2 + o.nH2);
+    BM_REQUIRE(std::isfinite(Fv), BM_ERR_NUMERIC, "bm_loss_grad: objective is not finite");
+    if (f) *f = o.f;
+    if (F) *F = Fv;
+    float* gWo = h->ix.transposed ? gH : gW;
+    float* gHo = h->ix.transposed ? gW : gH;
+    copy_out_rows(*h, gWo, h->gW.get(), h->ix.m, h->k);
+    copy_out_rows(*h, gHo, h->gH.get(), h->ix.n, h->k);
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+bm_status bm_bm_phase(bm_handle h, int32_t epochs, double* F) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    BM_REQUIRE(epochs >= 0, BM_ERR_INVALID, "bm_bm_phase: epochs must be >= 0");
+    bm_phase_dev(*h, epochs, F);
+  });
+}
+
+bm_status bm_init(bm_handle h, bm_prox_info* info) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] { init_step_dev(*h, info); });
+}
+
+bm_status bm_prox_step(bm_handle h, double alpha, bm_prox_info* info) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    const double a = alpha > 0 ? alpha : h->opt.alpha;
+    BM_REQUIRE(std::isfinite(a), BM_ERR_INVALID, "bm_prox_step: alpha must be finite");
+    prox_step_dev(*h, a, info);
+  });
+}
+
+bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
+  if (!h) return BM_ERR_INVALID;
+  bool converged = false;
+  bm_status st = guarded(h, [&] {
+    bm_solve_opts so{100, 0, 1e-10, 0.0, 0.0};
+    if (o) so = *o;
+    BM_REQUIRE(so.max_outer >= 0, BM_ERR_INVALID, "bm_solve: max_outer must be >= 0");
+    const auto t0 = std::chrono::steady_clock::now();
+    auto elapsed = [&] {
+      return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    bm_prox_info pi;
+    if (h->k == 0) init_step_dev(*h, &pi);
+    double F_prev = objective_now(*h);
+    double F = F_prev;
+    int outer = 0;
+    for (outer = 1; outer <= so.max_outer; ++outer) {
+      bm_phase_dev(*h, h->opt.bm_epochs, nullptr);
+      for (int x = 0; x < h->opt.pg_steps; ++x) prox_step_dev(*h, h->opt.alpha, &pi);
+      F = objective_now(*h);
+      BM_REQUIRE(std::isfinite(F), BM_ERR_NUMERIC, "bm_solve: objective is not finite");
+      if (so.F_target > 0 && F <= so.F_target) { converged = true; break; }
+      if (std::fabs(F_prev - F) / (1.0 + std::fabs(F_prev)) < so.tol) { converged = true; break; }
+      F_prev = F;
+      if (so.time_limit_s > 0 && elapsed() > so.time_limit_s) break;
+    }
+    if (info) {
+      info->outer = std::min(outer, so.max_outer);
+      info->k = h->k;
+      info->converged = converged ? 1 : 0;
+      info->F = F;
+      info->seconds = elapsed();
+    }
+  });
+  if (st == BM_OK && !converged) {
+    h->err = "bm_solve: stopped on max_outer or time_limit_s";
+    return BM_ERR_NOT_CONVERGED;
+  }
+  return st;
+}
+
+bm_status bm_profile_enable(bm_handle h, int32_t enable) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+    h->prof.marks.clear();
+    h->prof.used = 0;
+    h->prof.on = enable != 0;
+  });
+}
+
+bm_status bm_profile_read(bm_handle h, int32_t cap, char* names, int64_t* launches, double* total_ms,
+                          int32_t* count) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<std::string> keys;
+    std::vector<int64_t> cnt;
+    std::vector<double> ms;
+    for (auto& mk : h->prof.marks) {
+      if (!mk.second.second) continue;
+      float t = 0.f;
+      BM_CUDA(cudaEventElapsedTime(&t, mk.second.first, mk.second.second));
+      size_t i = 0;
+      while (i < keys.size() && keys[i] != mk.first) ++i;
+      if (i == keys.size()) keys.push_back(mk.first), cnt.push_back(0), ms.push_back(0.0);
+      cnt[i] += 1;
+      ms[i] += t;
+    }
+    if (count) *count = (int32_t)keys.size();
+    for (size_t i = 0; i < keys.size() && (int32_t)i < cap; ++i) {
+      if (names) {
+        std::snprintf(names + 48 * i, 48, "%s", keys[i].c_str());
+      }
+      if (launches) launches[i] = cnt[i];
+      if (total_ms) total_ms[i] = ms[i];
+    }
+  });
+}
+
+}  // extern "C"
+
+namespace bm {
+// exported for prox.cu
+void set_rank_ext(bm_ctx& h, int k) { set_rank(h, k); }
+double objective_ext(bm_ctx& h) { return objective_now(h); }
+}  // namespace bm

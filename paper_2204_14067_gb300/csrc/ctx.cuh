@@ -1,0 +1,123 @@
+// Handle state and the device routines shared between translation units.
+#pragma once
+#include "common.cuh"
+
+namespace bm {
+
+// Work split of one sparse pass: each segment is a run of at most kSegNnz
+// consecutive entries of one row (CSR) or column (CSC).  A warp processes one
+// segment; rows spanning several segments write partial sums that a fix-up
+// kernel adds in segment order (deterministic results).
+constexpr int64_t kSegNnz = 1024;
+
+struct Segs {
+  int64_t nseg = 0;
+  int64_t nmulti = 0;          // rows with more than one segment
+  DevBuf<int32_t> row;         // [nseg] owning row
+  DevBuf<int64_t> beg, end;    // [nseg] entry range
+  DevBuf<int32_t> slot;        // [nseg] partial slot (-1: single-segment row)
+  DevBuf<int32_t> mrow;        // [nmulti] row id
+  DevBuf<int32_t> mfirst;      // [nmulti] first partial slot
+  DevBuf<int32_t> mcount;      // [nmulti] number of partial slots
+  int64_t nslots = 0;
+};
+
+struct Index {
+  int64_t m = 0, n = 0, nnz = 0;  // internal orientation, m <= n
+  bool transposed = false;
+  DevBuf<int64_t> row_ptr, col_ptr;
+  DevBuf<int32_t> col, row;       // CSR column ids, CSC row ids
+  DevBuf<float> val, cval;        // A in CSR and in CSC order
+  DevBuf<int64_t> csr2csc;        // CSC position of CSR entry e
+  Segs rs, cs;                    // CSR (rows) and CSC (columns) work splits
+};
+
+// Scratch reused across calls (sized once for the handle's k_max).
+struct Scratch {
+  DevBuf<float> partial;          // segment partial sums
+  DevBuf<double> fseg;            // per-segment loss partials
+  DevBuf<double> red;             // block partials of dense reductions
+  DevBuf<double> scal;            // small device scalars
+};
+
+struct ProxState;  // defined in prox.cu
+
+// Optional per-kernel event timing (bm_profile_enable).
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  ~Profiler();
+  void begin(const char* name, cudaStream_t st);  // call before a launch
+  void end(cudaStream_t st);                      // call after it
+  cudaEvent_t next();
+};
+
+}  // namespace bm
+
+struct bm_ctx {
+  bm::Index ix;
+  double lambda = 0;
+  int k_max = 0;
+  bm_options opt{};
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  int k = 0;                     // current rank
+  int ld = 4;                    // leading dimension of W, H (round_up4(k), >= 4)
+  int ldmax = 4;                 // capacity: round_up4(k_max + 1)
+  bm::DevBuf<float> W, H;        // m x ld, n x ld (padding columns are zero)
+  bm::DevBuf<float> gW, gH;      // gradients
+  bm::DevBuf<float> DW, DH;      // BM search directions
+  bm::DevBuf<float> gWp, gHp;    // previous gradients (Polak-Ribiere)
+  bm::DevBuf<float> r_csr, r_csc;  // residual R on Omega in CSR / CSC order
+  bm::Scratch sc;
+  bm::ProxState* ps = nullptr;
+  bm::Profiler prof;
+  std::string err;
+  bool bm_changed = false;       // BM phase moved since the last PG step
+};
+
+namespace bm {
+
+// Wrap a kernel launch with profiler events when profiling is on.
+#define BM_LAUNCH(h, name, ...)                              \
+  do {                                                       \
+    if ((h).prof.on) (h).prof.begin(name, (h).stream);       \
+    __VA_ARGS__;                                             \
+    BM_CHECK_LAUNCH();                                       \
+    if ((h).prof.on) (h).prof.end((h).stream);               \
+  } while (0)
+
+// index.cu
+void build_index(bm_ctx& h, int64_t m, int64_t n, int64_t nnz, const int32_t* rows_d,
+                 const int32_t* cols_d, const float* vals_d);
+
+// grad.cu
+struct LossOut {
+  double f;      // 1/2 sum r^2
+  double nW2;    // ||W||^2
+  double nH2;    // ||H||^2
+};
+// f, gradients (written to h.gW/h.gH when want_grad), residual stored in
+// h.r_csr / h.r_csc when store_r.  Stream-ordered; returns after a sync.
+LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r);
+// Quartic coefficients c0..c4 of phi(s) along (h.DW, h.DH), using h.r_csr.
+void line_search_coeffs_dev(bm_ctx& h, double c[5]);
+// Dense helpers over m x ld / n x ld arrays (deterministic FP64 reductions).
+double dot_dev(bm_ctx& h, const float* x, const float* y, int64_t count);
+void axpy_dev(bm_ctx& h, float* y, const float* x, float a, int64_t count);          // y += a x
+void xpby_dev(bm_ctx& h, float* y, const float* x, float b, int64_t count);          // y = -x + b y
+void copy_pad_dev(bm_ctx& h, float* dst, int ldd, const float* src, int lds, int64_t rows,
+                  int cols, cudaMemcpyKind kind);
+
+// prox.cu
+void prox_create(bm_ctx& h);
+void prox_destroy(bm_ctx& h);
+void prox_reset(bm_ctx& h);
+void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info);
+void init_step_dev(bm_ctx& h, bm_prox_info* info);
+
+}  // namespace bm

@@ -1,0 +1,188 @@
+"""GPU parity of the index build and the sparse loss/gradient against the FP64 oracle.
+
+Index work must be bit-exact.  Floats: f, F within 1e-5 relative, gradients
+within 1e-5 in relative Frobenius norm (FP32 arithmetic with FP64 final
+reductions against FP64).
+"""
+import numpy as np
+import pytest
+
+from oracle import bm_oracle as O
+from synth import named_config, planted_uniform, random_factors
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def B():
+    import paper_2204_14067_gb300 as B
+    B.lib()
+    return B
+
+
+def _mk(B, p, k_max=None):
+    return B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, k_max or p.k_max)
+
+
+def _check_index(B, h, p):
+    ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
+    g = B.bm_get_index(h)
+    assert np.array_equal(g["row_ptr"], ix.row_ptr)
+    assert np.array_equal(g["col_ptr"], ix.col_ptr)
+    assert np.array_equal(g["col"], ix.col)
+    assert np.array_equal(g["row"], ix.row)
+    assert np.array_equal(g["val"], ix.val.astype(np.float32))
+    assert np.array_equal(g["cval"], ix.cval.astype(np.float32))
+    assert np.array_equal(g["csr2csc"], ix.csr2csc)
+    return ix
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("tiny", {}),
+    ("small", dict(m=3000, n=700, nnz=150_000, seed=3)),     # m > n: stored transposed
+    ("small", dict(m=700, n=3000, nnz=150_000, seed=4)),
+    ("small", dict(m=20_000, n=2_500, nnz=400_000, seed=6)),  # heavy rows -> multi-segment rows
+])
+def test_index_bit_exact(B, name, kw):
+    p = named_config(name, **kw)
+    if name == "small":
+        rng = np.random.default_rng(0)
+        perm = rng.permutation(p.nnz)
+        p.rows, p.cols, p.vals = p.rows[perm], p.cols[perm], p.vals[perm]
+    h = _mk(B, p)
+    try:
+        _check_index(B, h, p)
+    finally:
+        B.bm_destroy(h)
+
+
+def test_index_edge_cases(B):
+    # empty Omega, a single entry, empty rows and columns
+    for (m, n, rows, cols) in [(5, 9, [], []), (1, 1, [0], [0]), (6, 4, [5, 0, 5], [3, 0, 0]),
+                               (1, 7, [0, 0, 0], [6, 2, 4])]:
+        r = np.array(rows, np.int32)
+        c = np.array(cols, np.int32)
+        v = np.arange(1, len(rows) + 1, dtype=np.float32)
+        h = B.bm_create(m, n, r, c, v, 0.5, 1)
+        try:
+            ix = O.build_index(m, n, r, c, v)
+            g = B.bm_get_index(h)
+            assert np.array_equal(g["row_ptr"], ix.row_ptr) and np.array_equal(g["col_ptr"], ix.col_ptr)
+            assert np.array_equal(g["col"], ix.col) and np.array_equal(g["row"], ix.row)
+        finally:
+            B.bm_destroy(h)
+
+
+def test_create_rejects_invalid(B):
+    r = np.array([0, 0], np.int32)
+    c = np.array([1, 1], np.int32)
+    v = np.array([1, 2], np.float32)
+    with pytest.raises(B.BMError, match="repeated"):
+        B.bm_create(3, 3, r, c, v, 0.5, 1)
+    with pytest.raises(B.BMError, match="range"):
+        B.bm_create(3, 3, np.array([0, 3], np.int32), c, v, 0.5, 1)
+    with pytest.raises(B.BMError, match="non-finite"):
+        B.bm_create(3, 3, np.array([0, 1], np.int32), c, np.array([1, np.inf], np.float32), 0.5, 1)
+    with pytest.raises(B.BMError, match="lambda"):
+        B.bm_create(3, 3, np.array([0, 1], np.int32), c, v, -1.0, 1)
+    with pytest.raises(B.BMError, match="k_max"):
+        B.bm_create(3, 3, np.array([0, 1], np.int32), c, v, 0.5, 4)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 17, 33, 64, 100])
+@pytest.mark.parametrize("shape", [(3000, 700, 150_000), (20_000, 2_500, 400_000)])
+def test_loss_grad_parity(B, k, shape):
+    m, n, nnz = shape
+    p = named_config("small", m=m, n=n, nnz=nnz, seed=7, k_max=127)
+    h = _mk(B, p, k_max=min(127, m, n))
+    try:
+        W, H = random_factors(p.m, p.n, k, seed=k, scale=0.4)
+        B.bm_set_factors(h, k, W, H)
+        gW = np.empty_like(W)
+        gH = np.empty_like(H)
+        f, F = B.bm_loss_grad(h, gW, gH)
+        ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
+        W64, H64 = W.astype(np.float64), H.astype(np.float64)
+        Wi, Hi = (H64, W64) if ix.transposed else (W64, H64)
+        fo, Fo, gWo, gHo, _ = O.loss_grad(ix, Wi, Hi, p.lam)
+        if ix.transposed:
+            gWo, gHo = gHo, gWo
+        assert abs(f - fo) <= RTOL * fo
+        assert abs(F - Fo) <= RTOL * Fo
+        assert _rel(gW, gWo) <= RTOL
+        assert _rel(gH, gHo) <= RTOL
+    finally:
+        B.bm_destroy(h)
+
+
+def test_loss_grad_device_buffers_and_zero_rank(B):
+    torch = pytest.importorskip("torch")
+    p = planted_uniform(m=200, n=150, rank=3, frac=0.2, seed=2, lam=0.3)
+    h = _mk(B, p, k_max=10)
+    try:
+        f0, F0 = B.bm_loss_grad(h)       # k = 0: X = 0, f = 1/2 ||A||^2
+        assert abs(f0 - 0.5 * np.sum(p.vals.astype(np.float64) ** 2)) <= 1e-6 * f0
+        W, H = random_factors(p.m, p.n, 6, seed=1)
+        Wd, Hd = torch.from_numpy(W).cuda(), torch.from_numpy(H).cuda()
+        B.bm_set_factors(h, 6, Wd, Hd)
+        gWd, gHd = torch.empty_like(Wd), torch.empty_like(Hd)
+        f, F = B.bm_loss_grad(h, gWd, gHd)
+        gW, gH = np.empty_like(W), np.empty_like(H)
+        f2, F2 = B.bm_loss_grad(h, gW, gH)
+        assert f == f2 and F == F2
+        assert np.array_equal(gWd.cpu().numpy(), gW) and np.array_equal(gHd.cpu().numpy(), gH)
+        W2, H2 = B.bm_get_factors(h, p.m, p.n)
+        assert np.array_equal(W2, W) and np.array_equal(H2, H)
+    finally:
+        B.bm_destroy(h)
+
+
+def test_loss_grad_deterministic(B):
+    p = named_config("small", m=20_000, n=2_500, nnz=400_000, seed=6)
+    h = _mk(B, p)
+    try:
+        W, H = random_factors(p.m, p.n, 24, seed=5)
+        B.bm_set_factors(h, 24, W, H)
+        out = []
+        for _ in range(3):
+            gW, gH = np.empty_like(W), np.empty_like(H)
+            f, F = B.bm_loss_grad(h, gW, gH)
+            out.append((f, F, gW.tobytes(), gH.tobytes()))
+        assert out[0] == out[1] == out[2]
+    finally:
+        B.bm_destroy(h)
+
+
+def test_bm_phase_matches_oracle_and_is_monotone(B):
+    p = named_config("small", m=3000, n=700, nnz=150_000, seed=8)
+    h = _mk(B, p)
+    try:
+        k = 8
+        W, H = random_factors(p.m, p.n, k, seed=2, scale=0.3)
+        B.bm_set_factors(h, k, W, H)
+        ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
+        W64, H64 = W.astype(np.float64), H.astype(np.float64)
+        Wi, Hi = (H64, W64) if ix.transposed else (W64, H64)
+        st = O.State(W=Wi, H=Hi, U_prev=np.zeros((ix.m, 0)), U_prev2=None, u=None, psi=0.1,
+                     rank_hist=[0, 0], prev_warm_cols=0)
+        Fs = [B.bm_loss_grad(h)[1]]
+        for e in range(1, 7):
+            Fs.append(B.bm_bm_phase(h, 1))
+        st2, trace = O.bm_phase(ix, st, p.lam, 1)
+        Fo1 = O.objective(ix, st2.W, st2.H, p.lam)
+        assert abs(Fs[1] - Fo1) <= RTOL * Fo1
+        assert all(b <= a * (1 + 1e-6) for a, b in zip(Fs, Fs[1:]))
+        # three CG epochs in one call agree with the oracle's three epochs
+        B.bm_set_factors(h, k, W, H)
+        F3 = B.bm_bm_phase(h, 3)
+        st3, _ = O.bm_phase(ix, st, p.lam, 3)
+        Fo3 = O.objective(ix, st3.W, st3.H, p.lam)
+        assert abs(F3 - Fo3) <= 1e-4 * Fo3
+    finally:
+        B.bm_destroy(h)
