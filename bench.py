@@ -158,9 +158,12 @@ def run_ours(args):
     W0, H0 = random_factors(p.m, p.n, k, seed=11, scale=0.1)
     B.bm_set_factors(h, k, W0, H0)
 
+    gWd = torch.empty((p.m, k), dtype=torch.float32, device="cuda")
+    gHd = torch.empty((p.n, k), dtype=torch.float32, device="cuda")
+
     def step():
         if args.mode == "grad":
-            B.bm_loss_grad(h)
+            B.bm_loss_grad(h, gWd, gHd)
         else:
             B.bm_bm_phase(h, 3)
             B.bm_prox_step(h)

@@ -38,6 +38,9 @@ struct Scratch {
   DevBuf<double> fseg;            // per-segment loss partials
   DevBuf<double> red;             // block partials of dense reductions
   DevBuf<double> scal;            // small device scalars
+  DevBuf<int> sel_cols;           // column lists of small transforms
+  DevBuf<double> sel_scale;       // and their scales
+  DevBuf<double> eig_glob;        // eigensolver storage when a matrix exceeds shared memory
 };
 
 struct ProxState;  // defined in prox.cu

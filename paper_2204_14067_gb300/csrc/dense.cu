@@ -1,0 +1,746 @@
+// Thin dense blocks (Grams, thin products), the q-wide residual SpMM, the
+// one-CTA symmetric eigensolver and small helpers of the proximal step.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "dense.cuh"
+
+namespace bm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
+// ---------------------------------------------------------------- Gram C = A^T B
+constexpr int kGramThreads = 256;
+constexpr int kGramRows = 32;
+
+// Each block: a slab of rows, one group of 4x4 output micro-tiles per thread.
+// Within a tile of 32 rows sums are FP32 (compensated: Ogita-Rump-Oishi Dot2,
+// i.e. an error-free product and two-sum per term); tiles add into FP64.
+template <bool COMP>
+__global__ void __launch_bounds__(kGramThreads) k_gram(const float* __restrict__ A, int lda, int a,
+                                                       const float* __restrict__ B, int ldb, int b, int64_t L,
+                                                       int64_t slab, double* __restrict__ part) {
+  extern __shared__ float4 sm4[];
+  const int na = (a + 3) >> 2, nb = (b + 3) >> 2;
+  float4* As = sm4;
+  float4* Bs = sm4 + kGramRows * na;
+  const int mt = blockIdx.y * kGramThreads + threadIdx.x;
+  const bool active = mt < na * nb;
+  const int ti = active ? mt / nb : 0, tj = active ? mt % nb : 0;
+  double acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  const int64_t r0 = (int64_t)blockIdx.x * slab;
+  const int64_t r1 = min(L, r0 + slab);
+  for (int64_t rb = r0; rb < r1; rb += kGramRows) {
+    const int nr = (int)min((int64_t)kGramRows, r1 - rb);
+    for (int idx = threadIdx.x; idx < nr * na; idx += kGramThreads) {
+      const int r = idx / na, c = idx - r * na;
+      As[r * na + c] = ldg4(A + (rb + r) * lda + 4 * c);
+    }
+    for (int idx = threadIdx.x; idx < nr * nb; idx += kGramThreads) {
+      const int r = idx / nb, c = idx - r * nb;
+      Bs[r * nb + c] = ldg4(B + (rb + r) * ldb + 4 * c);
+    }
+    __syncthreads();
+    if (active) {
+      float s[16], lo[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) s[q] = 0.f, lo[q] = 0.f;
+      for (int r = 0; r < nr; ++r) {
+        const float4 av = As[r * na + ti];
+        const float4 bv = Bs[r * nb + tj];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float x = comp(av, p), y = comp(bv, q);
+            if (COMP) {
+              const float pr = x * y;
+              const float pe = fmaf(x, y, -pr);
+              const float t = s[p * 4 + q] + pr;
+              const float z = t - s[p * 4 + q];
+              const float err = (s[p * 4 + q] - (t - z)) + (pr - z);
+              s[p * 4 + q] = t;
+              lo[p * 4 + q] += err + pe;
+            } else {
+              s[p * 4 + q] = fmaf(x, y, s[p * 4 + q]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] += (double)s[q] + (double)lo[q];
+    }
+    __syncthreads();
+  }
+  if (active) {
+    double* out = part + (int64_t)blockIdx.x * a * b;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * ti + p, j = 4 * tj + q;
+        if (i < a && j < b) out[i * b + j] = acc[p * 4 + q];
+      }
+  }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int slabs, int ab, double* __restrict__ C) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ab; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < slabs; ++g) s += part[(int64_t)g * ab + e];
+    C[e] = s;
+  }
+}
+
+// ---------------------------------------------------------------- Y = beta Y + gamma A C
+constexpr int kGemmThreads = 256;
+
+__global__ void __launch_bounds__(kGemmThreads) k_gemm(const float* __restrict__ A, int lda, int a,
+                                                       const float* __restrict__ C, int ldc, int b,
+                                                       float* __restrict__ Y, int ldy, int64_t L, float beta,
+                                                       float gamma) {
+  extern __shared__ float4 gsm[];
+  const int nb4 = (b + 3) >> 2, a4 = (a + 3) >> 2;
+  const int rpb = kGemmThreads / nb4;
+  float4* Cs = gsm;                  // a x nb4
+  float* As = reinterpret_cast<float*>(gsm + (size_t)a * nb4);  // rpb x (4*a4)
+  for (int idx = threadIdx.x; idx < a * nb4; idx += kGemmThreads) {
+    const int t = idx / nb4, c = idx - t * nb4;
+    float4 v;
+    v.x = 4 * c + 0 < b ? C[t * ldc + 4 * c + 0] : 0.f;
+    v.y = 4 * c + 1 < b ? C[t * ldc + 4 * c + 1] : 0.f;
+    v.z = 4 * c + 2 < b ? C[t * ldc + 4 * c + 2] : 0.f;
+    v.w = 4 * c + 3 < b ? C[t * ldc + 4 * c + 3] : 0.f;
+    Cs[idx] = v;
+  }
+  const int rr = threadIdx.x / nb4, cj = threadIdx.x - rr * nb4;
+  for (int64_t r0 = (int64_t)blockIdx.x * rpb; r0 < L; r0 += (int64_t)gridDim.x * rpb) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < rpb * a4; idx += kGemmThreads) {
+      const int r = idx / a4, c = idx - r * a4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r0 + r < L) v = ldg4(A + (r0 + r) * lda + 4 * c);
+      reinterpret_cast<float4*>(As)[idx] = v;
+    }
+    __syncthreads();
+    if (rr < rpb && r0 + rr < L) {
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float* ar = As + rr * 4 * a4;
+      for (int t = 0; t < a; ++t) {
+        const float x = ar[t];
+        const float4 cv = Cs[t * nb4 + cj];
+        acc.x = fmaf(x, cv.x, acc.x);
+        acc.y = fmaf(x, cv.y, acc.y);
+        acc.z = fmaf(x, cv.z, acc.z);
+        acc.w = fmaf(x, cv.w, acc.w);
+      }
+      float4* yp = reinterpret_cast<float4*>(Y + (r0 + rr) * ldy + 4 * cj);
+      float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (beta != 0.f) y = *yp;
+      y.x = fmaf(gamma, acc.x, beta * y.x);
+      y.y = fmaf(gamma, acc.y, beta * y.y);
+      y.z = fmaf(gamma, acc.z, beta * y.z);
+      y.w = fmaf(gamma, acc.w, beta * y.w);
+      *yp = y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- q-wide SpMM of the residual
+struct SpArgs {
+  const int32_t* seg_row;
+  const int64_t* seg_beg;
+  const int64_t* seg_end;
+  const int32_t* seg_slot;
+  int64_t nseg;
+  const int32_t* idx;
+  const float* val;
+  const float* X;
+  int ldx, nchunk;
+  float* out;
+  int ldo;
+  float* partial;
+  int ldp;
+  float gamma;
+};
+
+template <int V>
+__global__ void __launch_bounds__(256) k_spmm(SpArgs a) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < a.nseg; s += nwarps) {
+    const int i = a.seg_row[s];
+    const int64_t beg = a.seg_beg[s], end = a.seg_end[s];
+    float4 acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool valid = e < end;
+      const int j = valid ? __ldg(a.idx + e) : 0;
+      const float vv = valid ? __ldg(a.val + e) : 0.f;
+#pragma unroll 2
+      for (int t = 0; t < 4; ++t) {
+        const int src = t * 8 + g;
+        const int jj = __shfl_sync(kFull, j, src);
+        const float w = __shfl_sync(kFull, vv, src);
+        const float* xr = a.X + (int64_t)jj * a.ldx;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int c = l + 4 * v;
+          if (c < a.nchunk) {
+            const float4 x = ldg4(xr + 4 * c);
+            acc[v].x = fmaf(w, x.x, acc[v].x);
+            acc[v].y = fmaf(w, x.y, acc[v].y);
+            acc[v].z = fmaf(w, x.z, acc[v].z);
+            acc[v].w = fmaf(w, x.w, acc[v].w);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+#pragma unroll
+      for (int m = 4; m < 32; m <<= 1) {
+        acc[v].x += __shfl_xor_sync(kFull, acc[v].x, m);
+        acc[v].y += __shfl_xor_sync(kFull, acc[v].y, m);
+        acc[v].z += __shfl_xor_sync(kFull, acc[v].z, m);
+        acc[v].w += __shfl_xor_sync(kFull, acc[v].w, m);
+      }
+    }
+    if (g == 0) {
+      const int slot = a.seg_slot[s];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int c = l + 4 * v;
+        if (c < a.nchunk) {
+          if (slot < 0) {
+            float4* op = reinterpret_cast<float4*>(a.out + (int64_t)i * a.ldo + 4 * c);
+            float4 o = *op;
+            o.x = fmaf(a.gamma, acc[v].x, o.x);
+            o.y = fmaf(a.gamma, acc[v].y, o.y);
+            o.z = fmaf(a.gamma, acc[v].z, o.z);
+            o.w = fmaf(a.gamma, acc[v].w, o.w);
+            *op = o;
+          } else {
+            *reinterpret_cast<float4*>(a.partial + (int64_t)slot * a.ldp + 4 * c) = acc[v];
+          }
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_spmm_fixup(const int32_t* __restrict__ mrow, const int32_t* __restrict__ mfirst,
+                             const int32_t* __restrict__ mcount, int64_t nmulti, const float* __restrict__ partial,
+                             int ldp, int cols, float gamma, float* __restrict__ out, int ldo) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nmulti * cols;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / cols;
+    const int c = (int)(t - q * cols);
+    const int64_t f = mfirst[q];
+    float s = 0.f;
+    for (int u = 0; u < mcount[q]; ++u) s += partial[(f + u) * ldp + c];
+    float* o = out + (int64_t)mrow[q] * ldo + c;
+    *o = fmaf(gamma, s, *o);
+  }
+}
+
+// ---------------------------------------------------------------- symmetric eigensolver
+constexpr int kEigMax = 256;
+constexpr int kEigThreads = 512;
+
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// Householder reduction to tridiagonal form (Golub & Van Loan, Sec. 8.3.1),
+// accumulation of Q, then the implicit-shift QL iteration on the tridiagonal
+// matrix; the rotations of each sweep are computed by one thread and applied
+// by all threads to the rows of Z^T.  Eigenvalues leave sorted descending.
+template <typename T>
+__global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restrict__ S, int n,
+                                                         double* __restrict__ evals, double* __restrict__ evecs,
+                                                         T* gA, T* gZ, int a_smem, int z_smem,
+                                                         int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char eig_raw[];
+  __shared__ T d[kEigMax], e[kEigMax], vv[kEigMax], pp[kEigMax], bet[kEigMax], cs[kEigMax], sn[kEigMax];
+  __shared__ T red[32];
+  __shared__ int sh_m, sh_cnt, sh_state;
+  T* A = a_smem ? reinterpret_cast<T*>(eig_raw) : gA;
+  T* Z = z_smem ? reinterpret_cast<T*>(eig_raw) + (a_smem ? (size_t)n * n : 0) : gZ;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const T eps = sizeof(T) == 8 ? (T)DBL_EPSILON : (T)FLT_EPSILON;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx - i * n;
+    A[idx] = (T)(0.5 * (S[i * n + j] + S[j * n + i]));
+  }
+  __syncthreads();
+  // ---- tridiagonalisation
+  for (int k = 0; k + 2 < n; ++k) {
+    const int L = n - k - 1;
+    T x = tid < L ? A[(k + 1 + tid) * n + k] : (T)0;
+    const T ss = block_sum<T>(x * x, red);
+    const T x0 = A[(k + 1) * n + k];
+    const T alpha = ss > 0 ? (x0 > 0 ? -sqrt(ss) : sqrt(ss)) : (T)0;
+    const T v0 = x0 - alpha;
+    const T vtv = ss - x0 * x0 + v0 * v0;
+    const T beta = vtv > 0 ? (T)2 / vtv : (T)0;
+    if (tid < L) {
+      const T v = tid == 0 ? v0 : x;
+      vv[tid] = v;
+      A[(k + 1 + tid) * n + k] = v;  // Householder vector kept in column k
+    }
+    if (tid == 0) {
+      bet[k] = beta;
+      d[k] = A[k * n + k];
+      e[k] = alpha;
+    }
+    __syncthreads();
+    if (beta != (T)0) {
+      if (tid < L) {
+        T acc = 0;
+        for (int c = 0; c < L; ++c) acc += A[(k + 1 + c) * n + (k + 1 + tid)] * vv[c];
+        pp[tid] = beta * acc;
+      }
+      __syncthreads();
+      const T Kc = (T)0.5 * beta * block_sum<T>(tid < L ? vv[tid] * pp[tid] : (T)0, red);
+      if (tid < L) pp[tid] -= Kc * vv[tid];
+      __syncthreads();
+      for (int idx = tid; idx < L * L; idx += nt) {
+        const int r = idx / L, c = idx - r * L;
+        A[(k + 1 + r) * n + (k + 1 + c)] -= vv[r] * pp[c] + pp[r] * vv[c];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[(n - 2) * n + (n - 2)];
+      e[n - 2] = A[(n - 1) * n + (n - 2)];
+    }
+    d[n - 1] = A[(n - 1) * n + (n - 1)];
+    e[n - 1] = 0;
+  }
+  __syncthreads();
+  // ---- Q = H_0 H_1 ... H_{n-3}, kept as Z^T (row i = column i of Q)
+  // Z may alias A's storage only when A is in global memory and Z in shared; the
+  // Householder vectors are read from A, so Z is separate storage here.
+  for (int idx = tid; idx < n * n; idx += nt) Z[idx] = (idx / n == idx % n) ? (T)1 : (T)0;
+  __syncthreads();
+  for (int k = n - 3; k >= 0; --k) {
+    const int L = n - k - 1;
+    if (tid < L) vv[tid] = A[(k + 1 + tid) * n + k];
+    __syncthreads();
+    const T beta = bet[k];
+    if (beta != (T)0) {
+      // rows j >= k+1 of Z^T: t_j = sum_c Z^T[j][k+1+c] v_c; Z^T[j][k+1+c] -= beta t_j v_c
+      for (int j = k + 1 + tid; j < n; j += nt) {
+        T t = 0;
+        for (int c = 0; c < L; ++c) t += Z[j * n + k + 1 + c] * vv[c];
+        t *= beta;
+        for (int c = 0; c < L; ++c) Z[j * n + k + 1 + c] -= t * vv[c];
+      }
+    }
+    __syncthreads();
+  }
+  // ---- implicit QL with shifts
+  if (tid == 0) sh_state = 0;
+  __syncthreads();
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    while (true) {
+      if (tid == 0) {
+        int m = l;
+        for (; m < n - 1; ++m) {
+          const T dd = fabs(d[m]) + fabs(d[m + 1]);
+          if (fabs(e[m]) <= eps * dd) break;
+        }
+        sh_m = m;
+        sh_cnt = 0;
+        if (m != l) {
+          if (++iter > 60) {
+            sh_state = 1;
+            sh_m = l;
+          } else {
+            T g = (d[l + 1] - d[l]) / ((T)2 * e[l]);
+            T r = hypot(g, (T)1);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
+            T s = 1, c = 1, p = 0;
+            bool early = false;
+            int cnt = 0;
+            for (int i = m - 1; i >= l; --i) {
+              const T f = s * e[i], b = c * e[i];
+              r = hypot(f, g);
+              e[i + 1] = r;
+              if (r == (T)0) {
+                d[i + 1] -= p;
+                e[m] = 0;
+                early = true;
+                break;
+              }
+              s = f / r;
+              c = g / r;
+              g = d[i + 1] - p;
+              r = (d[i] - g) * s + (T)2 * c * b;
+              p = s * r;
+              d[i + 1] = g + p;
+              g = c * r - b;
+              cs[cnt] = c;
+              sn[cnt] = s;
+              ++cnt;
+            }
+            if (!early) {
+              d[l] -= p;
+              e[l] = g;
+              e[m] = 0;
+            }
+            sh_cnt = cnt;
+          }
+        }
+      }
+      __syncthreads();
+      const int m = sh_m, cnt = sh_cnt;
+      if (m == l) break;
+      for (int q = tid; q < n; q += nt) {
+        for (int t = 0; t < cnt; ++t) {
+          const int i = m - 1 - t;
+          const T zi = Z[i * n + q], zf = Z[(i + 1) * n + q];
+          Z[(i + 1) * n + q] = sn[t] * zi + cs[t] * zf;
+          Z[i * n + q] = cs[t] * zi - sn[t] * zf;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- sort descending and write out
+  for (int i = tid; i < n; i += nt) {
+    const T di = d[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const T dj = d[j];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    evals[rank] = (double)di;
+    if (!isfinite((double)di)) atomicOr(status, 2);
+    for (int q = 0; q < n; ++q) evecs[q * n + rank] = (double)Z[i * n + q];
+  }
+  if (tid == 0 && sh_state) atomicOr(status, 1);
+}
+
+// ---------------------------------------------------------------- small helpers
+__global__ void k_select_scale(const double* __restrict__ E, int n, int rows, const int* __restrict__ cols,
+                               const double* __restrict__ scale, int ncols, float* __restrict__ T, int ldt) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * ldt; idx += gridDim.x * blockDim.x) {
+    const int r = idx / ldt, c = idx - r * ldt;
+    T[idx] = c < ncols ? (float)(E[r * n + cols[c]] * scale[c]) : 0.f;
+  }
+}
+
+__global__ void k_to_f32(const double* __restrict__ S, int rows, int cols, int lds, float* __restrict__ T, int ldt) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * ldt; idx += gridDim.x * blockDim.x) {
+    const int r = idx / ldt, c = idx - r * ldt;
+    T[idx] = c < cols ? (float)S[r * lds + c] : 0.f;
+  }
+}
+
+__global__ void k_small_mm(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
+                           int r, int s, int t, int transB) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r * t; idx += gridDim.x * blockDim.x) {
+    const int i = idx / t, j = idx - i * t;
+    double acc = 0.0;
+    for (int k = 0; k < s; ++k) acc += A[i * s + k] * (transB ? B[j * s + k] : B[k * t + j]);
+    C[idx] = acc;
+  }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+// SplitMix64 counter generator: key = mix(seed*gamma + stream),
+// u_i = ((mix(key + i*gamma) >> 11) + 1) 2^-53, x_j = sqrt(-2 ln u_2j) cos(2 pi u_2j+1)
+__global__ void k_counter_normal(uint64_t seed, uint64_t stream, uint64_t offset, int64_t count,
+                                 float* __restrict__ X, int ld, int col) {
+  const uint64_t G = 0x9E3779B97F4A7C15ull;
+  const uint64_t key = mix64(seed * G + stream);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t j = offset + (uint64_t)i;
+    const uint64_t z1 = mix64(key + (2 * j) * G), z2 = mix64(key + (2 * j + 1) * G);
+    const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = ((double)(z2 >> 11) + 1.0) * 0x1.0p-53;
+    X[i * ld + col] = (float)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+  }
+}
+
+__global__ void k_negate(const float* __restrict__ a, float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = -a[i];
+}
+
+__global__ void k_res_sums(const float* __restrict__ r, const float* __restrict__ a, int64_t n,
+                           double* __restrict__ part) {
+  __shared__ double s1[256], s2[256];
+  double x = 0.0, y = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double rv = r[i];
+    x += rv * rv;
+    y += rv * (double)a[i];
+  }
+  s1[threadIdx.x] = x;
+  s2[threadIdx.x] = y;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s1[threadIdx.x] += s1[threadIdx.x + o], s2[threadIdx.x] += s2[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = s1[0], part[2 * blockIdx.x + 1] = s2[0];
+}
+
+__global__ void k_sum_pairs(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int i = 0; i < nb; ++i) a += part[2 * i], b += part[2 * i + 1];
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+__global__ void k_copy_cols(const float* __restrict__ src, int lds, int s0, float* __restrict__ dst, int ldd,
+                            int d0, int c, int64_t rows) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < rows * c;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / c;
+    const int j = (int)(idx - r * c);
+    dst[r * ldd + d0 + j] = src[r * lds + s0 + j];
+  }
+}
+
+int grid1(int64_t work, int threads = 256) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, threads), (int64_t)num_sms() * 8));
+}
+
+template <int V>
+void launch_spmm(const SpArgs& a, int grid, cudaStream_t st) {
+  k_spmm<V><<<grid, 256, 0, st>>>(a);
+}
+
+}  // namespace
+
+void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, bool compensated, const char* tag) {
+  BM_REQUIRE(A.rows == B.rows, BM_ERR_INVALID, "gram: row mismatch");
+  const int a = A.cols, b = B.cols;
+  if (a == 0 || b == 0) return;
+  const int64_t L = A.rows;
+  if (L == 0) {
+    BM_CUDA(cudaMemsetAsync(C, 0, (size_t)a * b * sizeof(double), h.stream));
+    return;
+  }
+  const int na = (a + 3) / 4, nb = (b + 3) / 4;
+  int64_t gx = std::min<int64_t>(ceil_div(L, 64), (int64_t)2 * num_sms());
+  int64_t slab = ceil_div(ceil_div(L, gx), kGramRows) * kGramRows;
+  gx = ceil_div(L, slab);
+  const int gy = (int)ceil_div((int64_t)na * nb, kGramThreads);
+  w.gram_part.alloc((size_t)gx * a * b);
+  const size_t smem = (size_t)kGramRows * (na + nb) * sizeof(float4);
+  dim3 grid((unsigned)gx, (unsigned)gy);
+  if (compensated) {
+    BM_LAUNCH(h, tag, k_gram<true><<<grid, kGramThreads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab,
+                                                                        w.gram_part.get()));
+  } else {
+    BM_LAUNCH(h, tag, k_gram<false><<<grid, kGramThreads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab,
+                                                                         w.gram_part.get()));
+  }
+  BM_LAUNCH(h, "gram_reduce", k_gram_reduce<<<grid1(a * b), 256, 0, h.stream>>>(w.gram_part.get(), (int)gx, a * b, C));
+}
+
+void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, float beta, float gamma,
+              const char* tag) {
+  const int a = A.cols, b = Y.cols;
+  if (b == 0 || A.rows == 0) return;
+  if (a == 0) {
+    if (beta == 0.f) zero_dev(h, Y);
+    return;
+  }
+  const int nb4 = (b + 3) / 4, a4 = (a + 3) / 4;
+  BM_REQUIRE(nb4 <= kGemmThreads, BM_ERR_INVALID, "gemm: too many columns");
+  const int rpb = kGemmThreads / nb4;
+  const size_t smem = (size_t)a * nb4 * sizeof(float4) + (size_t)rpb * a4 * sizeof(float4);
+  static bool attr = false;
+  if (!attr) {
+    BM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  BM_REQUIRE(smem <= 200 * 1024, BM_ERR_INVALID, "gemm: block too large");
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A.rows, rpb), (int64_t)num_sms() * 8));
+  BM_LAUNCH(h, tag, k_gemm<<<grid, kGemmThreads, smem, h.stream>>>(A.p, A.ld, a, C, ldc, b, Y.p, Y.ld, A.rows,
+                                                                   beta, gamma));
+}
+
+void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall& Out, float gamma) {
+  const Index& ix = h.ix;
+  const Segs& sg = csr ? ix.rs : ix.cs;
+  if (X.cols == 0) return;
+  SpArgs a;
+  a.seg_row = sg.row.get();
+  a.seg_beg = sg.beg.get();
+  a.seg_end = sg.end.get();
+  a.seg_slot = sg.slot.get();
+  a.nseg = sg.nseg;
+  a.idx = csr ? ix.col.get() : ix.row.get();
+  a.val = vals;
+  a.X = X.p;
+  a.ldx = X.ld;
+  a.nchunk = (X.cols + 3) / 4;
+  a.out = Out.p;
+  a.ldo = Out.ld;
+  a.partial = h.sc.partial.get();
+  a.ldp = ((X.cols + 3) / 4) * 4;
+  a.gamma = gamma;
+  BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ldp <= (int64_t)h.sc.partial.n, BM_ERR_INVALID,
+             "spmm: partial buffer too small");
+  const int V = std::max(1, (a.nchunk + 3) / 4);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(sg.nseg, 8), (int64_t)num_sms() * 16));
+  const char* tag = csr ? "spmm_csr" : "spmm_csc";
+  switch (V) {
+    case 1: BM_LAUNCH(h, tag, launch_spmm<1>(a, grid, h.stream)); break;
+    case 2: BM_LAUNCH(h, tag, launch_spmm<2>(a, grid, h.stream)); break;
+    case 3: BM_LAUNCH(h, tag, launch_spmm<3>(a, grid, h.stream)); break;
+    case 4: BM_LAUNCH(h, tag, launch_spmm<4>(a, grid, h.stream)); break;
+    case 5: BM_LAUNCH(h, tag, launch_spmm<5>(a, grid, h.stream)); break;
+    case 6: BM_LAUNCH(h, tag, launch_spmm<6>(a, grid, h.stream)); break;
+    case 7: BM_LAUNCH(h, tag, launch_spmm<7>(a, grid, h.stream)); break;
+    case 8: BM_LAUNCH(h, tag, launch_spmm<8>(a, grid, h.stream)); break;
+    default: throw Error{BM_ERR_INVALID, "spmm: more than 128 columns"};
+  }
+  if (sg.nmulti) {
+    BM_LAUNCH(h, "spmm_fixup",
+              k_spmm_fixup<<<grid1(sg.nmulti * X.cols), 256, 0, h.stream>>>(
+                  sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti, a.partial, a.ldp, X.cols, gamma,
+                  Out.p, Out.ld));
+  }
+}
+
+void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, bool dbl) {
+  BM_REQUIRE(n >= 1 && n <= kEigMax, BM_ERR_INVALID, "eigensolver: size out of range");
+  const size_t es = dbl ? 8 : 4;
+  const size_t nn = (size_t)n * n * es;
+  const size_t cap = 200 * 1024;
+  int a_sm = 0, z_sm = 0;
+  if (2 * nn <= cap) a_sm = z_sm = 1;
+  else if (nn <= cap) a_sm = 1;
+  w.status.alloc(1);
+  BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
+  DevBuf<double>& gbuf = h.sc.eig_glob;  // global storage when shared memory is too small
+  if (!(a_sm && z_sm)) gbuf.alloc(2 * (size_t)kEigMax * kEigMax);
+  const size_t smem = (a_sm + z_sm) * nn;
+  if (dbl) {
+    static bool attr = false;
+    if (!attr) {
+      BM_CUDA(cudaFuncSetAttribute(k_sym_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+      attr = true;
+    }
+    double* gA = gbuf.get();
+    double* gZ = gbuf.get() ? gbuf.get() + (size_t)kEigMax * kEigMax : nullptr;
+    BM_LAUNCH(h, "sym_eig_f64", k_sym_eig<double><<<1, kEigThreads, smem, h.stream>>>(
+                                    S, n, evals, evecs, gA, gZ, a_sm, z_sm, w.status.get()));
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      BM_CUDA(cudaFuncSetAttribute(k_sym_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+      attr = true;
+    }
+    float* gA = reinterpret_cast<float*>(gbuf.get());
+    float* gZ = gA ? gA + (size_t)kEigMax * kEigMax : nullptr;
+    BM_LAUNCH(h, "sym_eig_f32", k_sym_eig<float><<<1, kEigThreads, smem, h.stream>>>(
+                                    S, n, evals, evecs, gA, gZ, a_sm, z_sm, w.status.get()));
+  }
+  int st = 0;
+  BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+  BM_CUDA(cudaStreamSynchronize(h.stream));
+  BM_REQUIRE(st == 0, BM_ERR_NUMERIC, st & 2 ? "eigensolver: non-finite eigenvalue" : "eigensolver: QL did not converge");
+}
+
+void select_scale_dev(bm_ctx& h, const double* E, int n, int rows, const int* cols_h, const double* scale_h,
+                      int cols, float* T, int ldt) {
+  DevBuf<int>& dcols = h.sc.sel_cols;
+  DevBuf<double>& dscale = h.sc.sel_scale;
+  dcols.alloc(std::max(cols, 1));
+  dscale.alloc(std::max(cols, 1));
+  if (cols) {
+    BM_CUDA(cudaMemcpyAsync(dcols.get(), cols_h, cols * sizeof(int), cudaMemcpyHostToDevice, h.stream));
+    BM_CUDA(cudaMemcpyAsync(dscale.get(), scale_h, cols * sizeof(double), cudaMemcpyHostToDevice, h.stream));
+  }
+  BM_LAUNCH(h, "small", k_select_scale<<<grid1(rows * ldt), 256, 0, h.stream>>>(E, n, rows, dcols.get(), dscale.get(),
+                                                                              cols, T, ldt));
+  BM_CUDA(cudaStreamSynchronize(h.stream));  // host arrays may go out of scope
+}
+
+void small_to_f32_dev(bm_ctx& h, const double* S, int rows, int cols, int lds, float* T, int ldt) {
+  if (rows == 0) return;
+  BM_LAUNCH(h, "small", k_to_f32<<<grid1(rows * ldt), 256, 0, h.stream>>>(S, rows, cols, lds, T, ldt));
+}
+
+void small_mm_dev(bm_ctx& h, const double* A, const double* B, double* C, int r, int s, int t, bool transB) {
+  if (r == 0 || t == 0) return;
+  BM_LAUNCH(h, "small", k_small_mm<<<grid1(r * t), 256, 0, h.stream>>>(A, B, C, r, s, t, transB ? 1 : 0));
+}
+
+void counter_normal_dev(bm_ctx& h, uint64_t seed, uint64_t stream, int64_t count, const Tall& X, int col) {
+  // offset: column c of a sketch uses counters [c*count, (c+1)*count)
+  BM_LAUNCH(h, "rng", k_counter_normal<<<grid1(count), 256, 0, h.stream>>>(seed, stream, (uint64_t)col * count,
+                                                                          count, X.p, X.ld, col));
+}
+
+void negate_values_dev(bm_ctx& h, const float* a, float* out, int64_t count) {
+  if (!count) return;
+  BM_LAUNCH(h, "negate", k_negate<<<grid1(count), 256, 0, h.stream>>>(a, out, count));
+}
+
+void residual_sums_dev(bm_ctx& h, const float* r, const float* a, int64_t nnz, double out[2]) {
+  const int nb = 304;
+  double* part = h.sc.red.get();
+  if (nnz == 0) {
+    out[0] = out[1] = 0;
+    return;
+  }
+  BM_LAUNCH(h, "res_sums", k_res_sums<<<nb, 256, 0, h.stream>>>(r, a, nnz, part));
+  BM_LAUNCH(h, "res_sums", k_sum_pairs<<<1, 32, 0, h.stream>>>(part, nb, h.sc.scal.get() + 8));
+  BM_CUDA(cudaMemcpyAsync(out, h.sc.scal.get() + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+  BM_CUDA(cudaStreamSynchronize(h.stream));
+}
+
+void copy_cols_dev(bm_ctx& h, const Tall& src, int s0, const Tall& dst, int d0, int c) {
+  if (c == 0 || src.rows == 0) return;
+  BM_LAUNCH(h, "copy_cols", k_copy_cols<<<grid1(src.rows * c), 256, 0, h.stream>>>(src.p, src.ld, s0, dst.p, dst.ld,
+                                                                                  d0, c, src.rows));
+}
+
+void zero_dev(bm_ctx& h, const Tall& X) {
+  if (X.rows == 0) return;
+  BM_CUDA(cudaMemsetAsync(X.p, 0, (size_t)X.rows * X.ld * sizeof(float), h.stream));
+}
+
+}  // namespace bm

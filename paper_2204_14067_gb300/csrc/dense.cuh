@@ -1,0 +1,70 @@
+// Dense thin-block routines used by the proximal step: Grams C = A^T B over a
+// long dimension, thin products Y = beta*Y + gamma*A*C, the q-wide SpMM of
+// the residual, the symmetric eigensolver and small helpers.
+#pragma once
+#include "ctx.cuh"
+
+namespace bm {
+
+// A tall row-major block: rows x cols with leading dimension ld (multiple of 4).
+struct Tall {
+  float* p = nullptr;
+  int64_t rows = 0;
+  int cols = 0;
+  int ld = 4;
+  float* row(int64_t i) const { return p + i * ld; }
+};
+
+// Scratch for the dense routines (owned by the prox state).
+struct DenseWork {
+  DevBuf<double> gram_part;   // slab partials of Grams
+  DevBuf<int> status;         // eigensolver status flags
+};
+
+// C (a x b, FP64, row-major ldc = b) = A^T B, A: L x a, B: L x b.
+// compensated: FP32 two-product/two-sum within a row tile (near-exact sums).
+void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, bool compensated,
+              const char* tag);
+
+// Y = beta * Y + gamma * A * C, A: L x a, C: a x b FP32 (row-major, ldc), Y: L x b.
+void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, float beta, float gamma,
+              const char* tag);
+
+// Sparse part of Z products: Out(i,:) += gamma * sum_e v_e X(idx_e,:) over a
+// segment split (CSR: i = row, idx = col; CSC: i = col, idx = row).
+void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall& Out, float gamma);
+
+// Symmetric eigendecomposition of S (n x n FP64, row-major, symmetrised on
+// load) in precision `dbl` (FP64) or FP32: eigenvalues descending into
+// evals[n] (FP64), eigenvectors into evecs (n x n FP64 row-major, column j
+// = vector j).  Throws BM_ERR_NUMERIC if the QL iteration fails.
+void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, bool dbl);
+
+// T (rows x cols FP32, ld) = E(0:rows, cols_idx) * diag(scale)  (E FP64 n x n)
+void select_scale_dev(bm_ctx& h, const double* E, int n, int rows, const int* cols_h, const double* scale_h,
+                      int cols, float* T, int ldt);
+
+// FP64 -> FP32 copy of a small matrix with new leading dimension.
+void small_to_f32_dev(bm_ctx& h, const double* S, int rows, int cols, int lds, float* T, int ldt);
+
+// C = A * B (FP64 small matrices, row-major, dims r x s times s x t) and
+// C = A * B^T (r x s times t x s).
+void small_mm_dev(bm_ctx& h, const double* A, const double* B, double* C, int r, int s, int t, bool transB);
+
+// x(count) = counter-based standard normals (SplitMix64 + Box-Muller, FP64) as FP32,
+// written into column `col` of the tall block.
+void counter_normal_dev(bm_ctx& h, uint64_t seed, uint64_t stream, int64_t count, const Tall& X, int col);
+
+// Fill `val` with -A (CSR and CSC order).
+void negate_values_dev(bm_ctx& h, const float* a, float* out, int64_t count);
+
+// sums over Omega: out[0] = sum r^2, out[1] = sum r*a  (CSR order)
+void residual_sums_dev(bm_ctx& h, const float* r, const float* a, int64_t nnz, double out[2]);
+
+// column copy: dst(:, d0:d0+c) = src(:, s0:s0+c)
+void copy_cols_dev(bm_ctx& h, const Tall& src, int s0, const Tall& dst, int d0, int c);
+
+// set all of a tall block to zero (rows x ld)
+void zero_dev(bm_ctx& h, const Tall& X);
+
+}  // namespace bm
