@@ -205,6 +205,33 @@ bm_status bm_prox_step(bm_handle h, double alpha, bm_prox_info* info);
 bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info);
 
 /*
+ * Distance-geometry (PSD) factorised loss, Eq. "EDM" of the supplement (BM
+ * formulation of the kernel-estimation / molecular-conformation QSDP):
+ *   g(V) = 1/2 sum_{(i,j) in Omega} w_ij (<E_ij, V V^T> - d_ij^2)^2 + lambda ||V||_F^2
+ *   grad g(V) = 2 (sum_{(i,j)} w_ij r_ij E_ij + lambda I) V
+ * with E_ij = (e_i - e_j)(e_i - e_j)^T, so <E_ij, V V^T> = ||v_i - v_j||^2,
+ * and r_ij = ||v_i - v_j||^2 - d_ij^2.  lambda may be negative (trace
+ * regulariser on the PSD cone).  Weights w_ij = 2 give the unhalved sum
+ * sum r_ij^2.
+ */
+typedef struct bm_edm_ctx* bm_edm_handle;
+
+/* n points (>= 2); npairs pairs (i[p], j[p]), 0 <= i, j < n, i != j, each
+ * unordered pair at most once; d[p] >= 0 finite; w[p] finite (w NULL: all 1).
+ * Arrays host or device, copied.  1 <= k_max <= min(128, n).  Builds a
+ * symmetric CSR (both directions of every pair) on the device.
+ * Errors: BM_ERR_INVALID for bad indices, repeated pairs, bad values. */
+bm_status bm_edm_create(int64_t n, int64_t npairs, const int32_t* i, const int32_t* j, const float* d,
+                        const float* w, double lambda, int32_t k_max, bm_edm_handle* out);
+void bm_edm_destroy(bm_edm_handle h);
+const char* bm_edm_last_error(bm_edm_handle h);
+/* V float[n*k] row-major (host or device), 1 <= k <= k_max. */
+bm_status bm_edm_set_factor(bm_edm_handle h, int32_t k, const float* V);
+/* *g (host, nullable) = g(V); gV float[n*k] (host or device, nullable) = grad g(V).
+ * Errors: BM_ERR_NUMERIC if g is not finite. */
+bm_status bm_edm_loss_grad(bm_edm_handle h, double* g, float* gV);
+
+/*
  * Kernel timing for measurement.  While enabled, the library records a pair
  * of CUDA events on the handle's stream around every launch of its kernels
  * (no extra synchronisation).  bm_profile_read synchronises, then reports per

@@ -580,3 +580,29 @@ def solve(ix: Index, lam: float, k_init: int, k_max: int, opt: Options = Options
 
 def problem_from_arrays(m, n, rows, cols, vals) -> Index:
     return build_index(m, n, rows, cols, vals)
+
+
+# ---------------------------------------------------------------------------
+# PSD / distance-geometry factorised loss (Eq. "EDM", supplement Sec. "The BM
+# formulations for the RKE problem and the molecular conformation problem")
+# ---------------------------------------------------------------------------
+def edm_loss_grad(V: np.ndarray, i: np.ndarray, j: np.ndarray, d: np.ndarray, w, lam: float):
+    """g(V) = 1/2 sum_{(i,j)} w_ij (<E_ij, V V^T> - d_ij^2)^2 + lam ||V||_F^2,
+    E_ij = (e_i - e_j)(e_i - e_j)^T, so <E_ij, V V^T> = ||v_i - v_j||^2;
+    grad g(V) = 2 (sum w_ij r_ij E_ij + lam I) V.  Returns (g, grad, r)."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    w = np.broadcast_to(np.asarray(w, dtype=np.float64), (i.shape[0],))
+    diff = V[i] - V[j]
+    r = np.sum(diff * diff, axis=1) - np.asarray(d, dtype=np.float64) ** 2
+    g = 0.5 * float(np.sum(w * r * r)) + lam * float(np.sum(V * V))
+    E = sp.coo_matrix((np.concatenate([w * r, w * r, -w * r, -w * r]),
+                       (np.concatenate([i, j, i, j]), np.concatenate([i, j, j, i]))),
+                      shape=(V.shape[0], V.shape[0])).tocsr()
+    grad = 2.0 * (E @ V) + 2.0 * lam * V
+    return g, np.asarray(grad), r
+
+
+def edm_lambda(n: int, d: np.ndarray) -> float:
+    """lambda = -10 sqrt(n) / sum d_ij^2 (the molecular-conformation setting)."""
+    return -10.0 * math.sqrt(n) / float(np.sum(np.asarray(d, dtype=np.float64) ** 2))

@@ -8,6 +8,10 @@ from .binding import (  # noqa: F401
     bm_default_options,
     bm_destroy,
     bm_dims,
+    bm_edm_create,
+    bm_edm_destroy,
+    bm_edm_loss_grad,
+    bm_edm_set_factor,
     bm_get_factors,
     bm_get_index,
     bm_init,

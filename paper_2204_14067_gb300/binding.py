@@ -245,3 +245,40 @@ def bm_profile_read(h, cap=64):
         nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (int(launches[i]), float(ms[i]))
     return out
+
+
+_SIGS.update({
+    "bm_edm_create": (_c.c_int, [_c.c_int64, _c.c_int64, _P, _P, _P, _P, _c.c_double, _c.c_int32,
+                                 _c.POINTER(_P)]),
+    "bm_edm_destroy": (None, [_P]),
+    "bm_edm_last_error": (_c.c_char_p, [_P]),
+    "bm_edm_set_factor": (_c.c_int, [_P, _c.c_int32, _P]),
+    "bm_edm_loss_grad": (_c.c_int, [_P, _P, _P]),
+})
+
+
+def _check_edm(status: int, h=None):
+    if status != BM_OK:
+        msg = lib().bm_edm_last_error(h)
+        raise BMError(status, msg.decode() if msg else "")
+
+
+def bm_edm_create(n, i, j, d, lam, k_max, w=None):
+    h = _P()
+    _check_edm(lib().bm_edm_create(int(n), int(i.shape[0]), _ptr(i), _ptr(j), _ptr(d), _ptr(w), float(lam),
+                                   int(k_max), ctypes.byref(h)))
+    return h.value
+
+
+def bm_edm_destroy(h):
+    lib().bm_edm_destroy(h)
+
+
+def bm_edm_set_factor(h, k, V):
+    _check_edm(lib().bm_edm_set_factor(h, int(k), _ptr(V)), h)
+
+
+def bm_edm_loss_grad(h, gV=None):
+    g = ctypes.c_double()
+    _check_edm(lib().bm_edm_loss_grad(h, ctypes.byref(g), _ptr(gV)), h)
+    return g.value

@@ -124,3 +124,13 @@ void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info);
 void init_step_dev(bm_ctx& h, bm_prox_info* info);
 
 }  // namespace bm
+
+namespace bm {
+// index.cu helpers shared with edm.cu
+void sort_pairs_ext(DevBuf<uint64_t>& k0, DevBuf<uint32_t>& v0, DevBuf<uint64_t>& k1, DevBuf<uint32_t>& v1,
+                    int64_t n, int bits, cudaStream_t st);
+void build_segs_ext(Segs& s, const DevBuf<int64_t>& ptr_d, int64_t rows, cudaStream_t st);
+void lower_bounds_ext(const uint64_t* keys, int64_t nnz, uint64_t stride, int64_t count, int64_t* ptr,
+                      cudaStream_t st);
+int key_bits_ext(uint64_t v);
+}  // namespace bm

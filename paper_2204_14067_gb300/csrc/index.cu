@@ -416,3 +416,20 @@ void build_index(bm_ctx& h, int64_t m, int64_t n, int64_t nnz, const int32_t* ro
 }
 
 }  // namespace bm
+
+namespace bm {
+// Shared with the distance-geometry index build (edm.cu).
+void sort_pairs_ext(DevBuf<uint64_t>& k0, DevBuf<uint32_t>& v0, DevBuf<uint64_t>& k1, DevBuf<uint32_t>& v1,
+                    int64_t n, int bits, cudaStream_t st) {
+  radix_sort_pairs(k0, v0, k1, v1, n, bits, st);
+}
+void build_segs_ext(Segs& s, const DevBuf<int64_t>& ptr_d, int64_t rows, cudaStream_t st) {
+  build_segs(s, ptr_d, rows, st);
+}
+void lower_bounds_ext(const uint64_t* keys, int64_t nnz, uint64_t stride, int64_t count, int64_t* ptr,
+                      cudaStream_t st) {
+  k_lower_bounds<<<grid_for(count + 1, 256), 256, 0, st>>>(keys, nnz, stride, count, ptr);
+  BM_CHECK_LAUNCH();
+}
+int key_bits_ext(uint64_t v) { return bits_for(v); }
+}  // namespace bm

@@ -139,7 +139,7 @@ int orth_dev(bm_ctx& h, const Tall& M, const Tall* F, const Tall* LM, const Tall
       if (LM) gemm_dev(h, *LF, ps.Ts.get(), ps.ldq2, mview(h, la, c1), 1.f, -1.f, "gemm_orth");
     }
     gram_dev(h, ps.dw, Mh, Mh, ps.G.get(), true, "gram_orth");
-    sym_eig_dev(h, ps.dw, ps.G.get(), c1, ps.ev.get(), ps.E.get(), true);
+    sym_eig_dev(h, ps.dw, ps.G.get(), c1, ps.ev.get(), ps.E.get(), false);  // FP32: drop test and scaling, pass 2 restores orthogonality
     std::vector<double> lam = to_host(h, ps.ev.get(), c1);
     std::vector<int> keep;
     std::vector<double> s;
@@ -224,7 +224,7 @@ LmsvdOut lmsvd_dev(bm_ctx& h, int c0, double alpha) {
       LQ = mview(h, kLQ, q);
     }
     gram_dev(h, ps.dw, Q, LQ, ps.G.get(), true, "gram_rr");
-    sym_eig_dev(h, ps.dw, ps.G.get(), q, ps.ev.get(), ps.E.get(), true);
+    sym_eig_dev(h, ps.dw, ps.G.get(), q, ps.ev.get(), ps.E.get(), false);  // FP32 Rayleigh-Ritz
     std::vector<double> th = to_host(h, ps.ev.get(), q);
     const int kk = std::min(k, q);
     std::vector<int> sel(kk);

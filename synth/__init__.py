@@ -10,4 +10,6 @@ from .gen import (  # noqa: F401
     zipf_ratings,
     named_config,
     random_factors,
+    PairProblem,
+    self_avoiding_chain,
 )

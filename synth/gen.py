@@ -259,3 +259,71 @@ def random_factors(m: int, n: int, k: int, seed: int, scale: float = 0.3):
     W = (scale * rng.standard_normal((m, k))).astype(np.float32)
     H = (scale * rng.standard_normal((n, k))).astype(np.float32)
     return W, H
+
+
+@dataclasses.dataclass
+class PairProblem:
+    """Distance data on a point set: pairs (i < j) with noisy distances d_ij."""
+
+    name: str
+    n: int
+    i: np.ndarray      # int32 [npairs]
+    j: np.ndarray      # int32 [npairs]
+    d: np.ndarray      # float32 [npairs]
+    X_true: np.ndarray  # float64 [n, 3]
+    seed: int
+    recipe: str
+
+    @property
+    def npairs(self) -> int:
+        return int(self.i.shape[0])
+
+
+def self_avoiding_chain(n=30_000, cutoff=6.0, noise=0.10, exclusion=1.0, seed=3, name="chain") -> PairProblem:
+    """3-D self-avoiding random walk with unit bonds; all pairs within `cutoff`.
+
+    Each step draws a direction uniformly on the sphere and is redrawn while
+    the new point lies within `exclusion` of any earlier, non-bonded point
+    (checked through a uniform grid of cell size `exclusion`).  Omega is every
+    pair i < j at true distance <= cutoff; d_ij = true * (1 + U(-noise, noise)).
+    """
+    import scipy.spatial
+
+    rng = _rng(seed, 4)
+    X = np.zeros((n, 3))
+    cells: dict = {}
+
+    def key(p):
+        return (int(np.floor(p[0] / exclusion)), int(np.floor(p[1] / exclusion)), int(np.floor(p[2] / exclusion)))
+
+    cells.setdefault(key(X[0]), []).append(0)
+    for t in range(1, n):
+        for _ in range(1000):
+            v = rng.standard_normal(3)
+            p = X[t - 1] + v / np.linalg.norm(v)
+            c = key(p)
+            ok = True
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        for q in cells.get((c[0] + dx, c[1] + dy, c[2] + dz), ()):
+                            if q != t - 1 and np.sum((X[q] - p) ** 2) < exclusion ** 2:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                break
+        X[t] = p
+        cells.setdefault(c, []).append(t)
+    tree = scipy.spatial.cKDTree(X)
+    pairs = np.array(sorted(tree.query_pairs(cutoff)), dtype=np.int64)
+    dtrue = np.sqrt(np.sum((X[pairs[:, 0]] - X[pairs[:, 1]]) ** 2, axis=1))
+    d = dtrue * (1.0 + rng.uniform(-noise, noise, size=dtrue.shape[0]))
+    return PairProblem(name, n, pairs[:, 0].astype(np.int32), pairs[:, 1].astype(np.int32), d.astype(np.float32),
+                       X, seed, f"3-D self-avoiding walk, unit bonds, exclusion {exclusion}, pairs within {cutoff}, "
+                                f"d = true*(1+U(-{noise},{noise}))")
