@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "dense.cuh"
+#include "pipe.cuh"
 
 namespace bm {
 namespace {
@@ -155,90 +156,6 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const float* __restrict__
 }
 
 // ---------------------------------------------------------------- q-wide SpMM of the residual
-struct SpArgs {
-  const int32_t* seg_row;
-  const int64_t* seg_beg;
-  const int64_t* seg_end;
-  const int32_t* seg_slot;
-  int64_t nseg;
-  const int32_t* idx;
-  const float* val;
-  const float* X;
-  int ldx, nchunk;
-  float* out;
-  int ldo;
-  float* partial;
-  int ldp;
-  float gamma;
-};
-
-template <int V>
-__global__ void __launch_bounds__(256) k_spmm(SpArgs a) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < a.nseg; s += nwarps) {
-    const int i = a.seg_row[s];
-    const int64_t beg = a.seg_beg[s], end = a.seg_end[s];
-    float4 acc[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t e0 = beg; e0 < end; e0 += 32) {
-      const int64_t e = e0 + lane;
-      const bool valid = e < end;
-      const int j = valid ? __ldg(a.idx + e) : 0;
-      const float vv = valid ? __ldg(a.val + e) : 0.f;
-#pragma unroll 2
-      for (int t = 0; t < 4; ++t) {
-        const int src = t * 8 + g;
-        const int jj = __shfl_sync(kFull, j, src);
-        const float w = __shfl_sync(kFull, vv, src);
-        const float* xr = a.X + (int64_t)jj * a.ldx;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const int c = l + 4 * v;
-          if (c < a.nchunk) {
-            const float4 x = ldg4(xr + 4 * c);
-            acc[v].x = fmaf(w, x.x, acc[v].x);
-            acc[v].y = fmaf(w, x.y, acc[v].y);
-            acc[v].z = fmaf(w, x.z, acc[v].z);
-            acc[v].w = fmaf(w, x.w, acc[v].w);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-#pragma unroll
-      for (int m = 4; m < 32; m <<= 1) {
-        acc[v].x += __shfl_xor_sync(kFull, acc[v].x, m);
-        acc[v].y += __shfl_xor_sync(kFull, acc[v].y, m);
-        acc[v].z += __shfl_xor_sync(kFull, acc[v].z, m);
-        acc[v].w += __shfl_xor_sync(kFull, acc[v].w, m);
-      }
-    }
-    if (g == 0) {
-      const int slot = a.seg_slot[s];
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int c = l + 4 * v;
-        if (c < a.nchunk) {
-          if (slot < 0) {
-            float4* op = reinterpret_cast<float4*>(a.out + (int64_t)i * a.ldo + 4 * c);
-            float4 o = *op;
-            o.x = fmaf(a.gamma, acc[v].x, o.x);
-            o.y = fmaf(a.gamma, acc[v].y, o.y);
-            o.z = fmaf(a.gamma, acc[v].z, o.z);
-            o.w = fmaf(a.gamma, acc[v].w, o.w);
-            *op = o;
-          } else {
-            *reinterpret_cast<float4*>(a.partial + (int64_t)slot * a.ldp + 4 * c) = acc[v];
-          }
-        }
-      }
-    }
-  }
-}
-
 __global__ void k_spmm_fixup(const int32_t* __restrict__ mrow, const int32_t* __restrict__ mfirst,
                              const int32_t* __restrict__ mcount, int64_t nmulti, const float* __restrict__ partial,
                              int ldp, int cols, float gamma, float* __restrict__ out, int ldo) {
@@ -284,6 +201,7 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
   __shared__ T d[kEigMax], e[kEigMax], vv[kEigMax], pp[kEigMax], bet[kEigMax], cs[kEigMax], sn[kEigMax];
   __shared__ T red[32];
   __shared__ int sh_m, sh_cnt, sh_state;
+  __shared__ T sh_anorm;
   T* A = a_smem ? reinterpret_cast<T*>(eig_raw) : gA;
   T* Z = z_smem ? reinterpret_cast<T*>(eig_raw) + (a_smem ? (size_t)n * n : 0) : gZ;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -362,7 +280,12 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
     __syncthreads();
   }
   // ---- implicit QL with shifts
-  if (tid == 0) sh_state = 0;
+  if (tid == 0) {
+    sh_state = 0;
+    T an = 0;
+    for (int i = 0; i < n; ++i) an = fmax(an, fabs(d[i]) + fabs(e[i]) + (i ? fabs(e[i - 1]) : (T)0));
+    sh_anorm = an;
+  }
   __syncthreads();
   for (int l = 0; l < n; ++l) {
     int iter = 0;
@@ -371,7 +294,9 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
         int m = l;
         for (; m < n - 1; ++m) {
           const T dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) <= eps * dd) break;
+          // relative test, with an absolute floor eps*||T|| so that (near) zero
+          // eigenvalues deflate as well
+          if (fabs(e[m]) <= eps * dd || fabs(e[m]) <= eps * sh_anorm) break;
         }
         sh_m = m;
         sh_cnt = 0;
@@ -542,11 +467,6 @@ int grid1(int64_t work, int threads = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, threads), (int64_t)num_sms() * 8));
 }
 
-template <int V>
-void launch_spmm(const SpArgs& a, int grid, cudaStream_t st) {
-  k_spmm<V><<<grid, 256, 0, st>>>(a);
-}
-
 }  // namespace
 
 void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, bool compensated, const char* tag) {
@@ -603,42 +523,29 @@ void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall&
   const Index& ix = h.ix;
   const Segs& sg = csr ? ix.rs : ix.cs;
   if (X.cols == 0) return;
-  SpArgs a;
+  PipeArgs a{};
   a.seg_row = sg.row.get();
   a.seg_beg = sg.beg.get();
   a.seg_end = sg.end.get();
   a.seg_slot = sg.slot.get();
   a.nseg = sg.nseg;
   a.idx = csr ? ix.col.get() : ix.row.get();
-  a.val = vals;
-  a.X = X.p;
-  a.ldx = X.ld;
+  a.scal = vals;
+  a.g0 = X.p;
+  a.ld = X.ld;
   a.nchunk = (X.cols + 3) / 4;
-  a.out = Out.p;
-  a.ldo = Out.ld;
-  a.partial = h.sc.partial.get();
-  a.ldp = ((X.cols + 3) / 4) * 4;
   a.gamma = gamma;
-  BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ldp <= (int64_t)h.sc.partial.n, BM_ERR_INVALID,
+  a.out = Out.p;
+  a.ld_out = Out.ld;
+  a.partial = h.sc.partial.get();
+  a.ld_part = 4 * a.nchunk;
+  BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ld_part <= (int64_t)h.sc.partial.n, BM_ERR_INVALID,
              "spmm: partial buffer too small");
-  const int V = std::max(1, (a.nchunk + 3) / 4);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(sg.nseg, 8), (int64_t)num_sms() * 16));
-  const char* tag = csr ? "spmm_csr" : "spmm_csc";
-  switch (V) {
-    case 1: BM_LAUNCH(h, tag, launch_spmm<1>(a, grid, h.stream)); break;
-    case 2: BM_LAUNCH(h, tag, launch_spmm<2>(a, grid, h.stream)); break;
-    case 3: BM_LAUNCH(h, tag, launch_spmm<3>(a, grid, h.stream)); break;
-    case 4: BM_LAUNCH(h, tag, launch_spmm<4>(a, grid, h.stream)); break;
-    case 5: BM_LAUNCH(h, tag, launch_spmm<5>(a, grid, h.stream)); break;
-    case 6: BM_LAUNCH(h, tag, launch_spmm<6>(a, grid, h.stream)); break;
-    case 7: BM_LAUNCH(h, tag, launch_spmm<7>(a, grid, h.stream)); break;
-    case 8: BM_LAUNCH(h, tag, launch_spmm<8>(a, grid, h.stream)); break;
-    default: throw Error{BM_ERR_INVALID, "spmm: more than 128 columns"};
-  }
+  BM_LAUNCH(h, csr ? "spmm_csr" : "spmm_csc", launch_pipe<1>(a, h.stream));
   if (sg.nmulti) {
     BM_LAUNCH(h, "spmm_fixup",
               k_spmm_fixup<<<grid1(sg.nmulti * X.cols), 256, 0, h.stream>>>(
-                  sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti, a.partial, a.ldp, X.cols, gamma,
+                  sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti, a.partial, a.ld_part, X.cols, gamma,
                   Out.p, Out.ld));
   }
 }
