@@ -232,6 +232,40 @@ bm_status bm_edm_set_factor(bm_edm_handle h, int32_t k, const float* V);
 bm_status bm_edm_loss_grad(bm_edm_handle h, double* g, float* gV);
 
 /*
+ * bm_loss_grad_csr_noalloc -- the loss and W-side gradient of (MF) for
+ * callers that cannot allocate device memory.  The paper has no counterpart;
+ * this exists for code that may not call cudaMalloc where it needs a
+ * gradient: kernels driven from inside another framework's memory pool,
+ * allocation-free real-time or graph-replay loops, and callers that only
+ * hold buffers handed to them.  It allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library call.  Its one scratch array (a loss
+ * partial per row) is a fixed file-scope device array of
+ * BM_NOALLOC_MAX_ROWS doubles (2 MiB) that every GPU loading the library
+ * keeps until the process exits.
+ *   m, n      matrix size (internal orientation, any m, n >= 1); m must not
+ *             exceed BM_NOALLOC_MAX_ROWS (else BM_ERR_INVALID).
+ *   row_ptr   int64[m+1], col int32[nnz], val float[nnz]: CSR of Omega and A
+ *             (columns < n; the arrays are trusted, not validated).
+ *   W, H      float[m*ld], float[n*ld] row-major, 1 <= k <= ld <= 128,
+ *             ld % 4 == 0; columns k..ld-1 must be zero.
+ *   gW        float[m*ld] out: R H + lambda W (columns k..ld-1 written as 0).
+ *   f         double* out (device): 1/2 sum r_e^2.
+ *   stream    cudaStream_t the work is queued on (NULL: default stream).
+ * Every pointer must be device memory.  The call is asynchronous: results
+ * are ready when `stream` reaches them.  The first call on a device looks up
+ * the scratch array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the scratch array and overwrites the rows it reads, so calls
+ * that overlap on the GPU (other streams, other threads) race; serialise them.
+ * Failures return a status; the message is in bm_noalloc_last_error().
+ */
+#define BM_NOALLOC_MAX_ROWS 262144
+bm_status bm_loss_grad_csr_noalloc(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                   const float* val, const float* W, const float* H, int32_t k, int32_t ld,
+                                   double lambda, float* gW, double* f, void* stream);
+const char* bm_noalloc_last_error(void);
+
+/*
  * Kernel timing for measurement.  While enabled, the library records a pair
  * of CUDA events on the handle's stream around every launch of its kernels
  * (no extra synchronisation).  bm_profile_read synchronises, then reports per

@@ -17,6 +17,7 @@ from .binding import (  # noqa: F401
     bm_init,
     bm_last_error,
     bm_loss_grad,
+    bm_loss_grad_csr_noalloc,
     bm_profile_enable,
     bm_profile_read,
     bm_prox_step,

@@ -15,7 +15,7 @@ import re
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libbm.so")
+LIB_PATH = os.environ.get("BM_LIB", os.path.join(HERE, "libbm.so"))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "bm.h")
 
 BM_OK, BM_ERR_INVALID, BM_ERR_OOM, BM_ERR_CUDA, BM_ERR_TIMEOUT, BM_ERR_NUMERIC, BM_ERR_NOT_CONVERGED = range(7)
@@ -282,3 +282,20 @@ def bm_edm_loss_grad(h, gV=None):
     g = ctypes.c_double()
     _check_edm(lib().bm_edm_loss_grad(h, ctypes.byref(g), _ptr(gV)), h)
     return g.value
+
+
+_SIGS.update({
+    "bm_loss_grad_csr_noalloc": (_c.c_int, [_c.c_int64, _c.c_int64, _P, _P, _P, _P, _P, _c.c_int32, _c.c_int32,
+                                            _c.c_double, _P, _P, _P]),
+    "bm_noalloc_last_error": (_c.c_char_p, []),
+})
+
+
+def bm_loss_grad_csr_noalloc(m, n, row_ptr, col, val, W, H, k, ld, lam, gW, f, stream=None):
+    """Allocation-free CSR loss/gradient; all arrays are CUDA tensors, f a 1-element float64 tensor."""
+    raw = getattr(stream, "cuda_stream", stream)
+    st = lib().bm_loss_grad_csr_noalloc(int(m), int(n), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(W), _ptr(H),
+                                         int(k), int(ld), float(lam), _ptr(gW), _ptr(f), raw)
+    if st != BM_OK:
+        msg = lib().bm_noalloc_last_error()
+        raise BMError(st, msg.decode() if msg else "")
