@@ -165,8 +165,7 @@ def run_ours(args):
         if args.mode == "grad":
             B.bm_loss_grad(h, gWd, gHd)
         else:
-            B.bm_bm_phase(h, 3)
-            B.bm_prox_step(h)
+            B.bm_solve(h, max_outer=1, tol=0.0)   # one cycle of Algorithm 1
 
     for _ in range(args.warmup):
         step()
@@ -208,8 +207,7 @@ def run_ours(args):
             gH = np.empty_like(Hh)
             B.bm_loss_grad(h, gW, gH)
         else:
-            B.bm_bm_phase(h, 3)
-            B.bm_prox_step(h)
+            B.bm_solve(h, max_outer=1, tol=0.0)
             Wh, Hh = B.bm_get_factors(h, p.m, p.n)
             kk = Wh.shape[1]
     torch.cuda.synchronize()

@@ -205,6 +205,74 @@ bm_status bm_prox_step(bm_handle h, double alpha, bm_prox_info* info);
 bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info);
 
 /*
+ * Batched BM phase over many solves.  A batch groups handles on one device
+ * (same precision mode, each with rank >= 1).  bm_batch_bm_phase runs
+ * `epochs` iterations of the BM-phase solver of bm_bm_phase on every handle
+ * in lockstep: each sparse pass (loss/gradient CSR and CSC, exact line
+ * search) of all handles with the same row width is one launch over their
+ * concatenated segment lists, and the direction, step length and update run
+ * as batched device kernels, so an epoch is one CUDA graph replay (captured
+ * on first use and re-captured when a rank changes).  F (double[count],
+ * nullable) receives each handle's objective after the last iteration.
+ * The batch owns a stream; the handles' own streams are synchronised first.
+ * A handle must not be used elsewhere while its batch call runs, and must
+ * outlive the batch.
+ */
+typedef struct bm_batch_ctx* bm_batch;
+bm_status bm_batch_create(bm_handle* hs, int32_t count, bm_batch* out);
+void bm_batch_destroy(bm_batch b);
+const char* bm_batch_last_error(bm_batch b);
+bm_status bm_batch_bm_phase(bm_batch b, int32_t epochs, double* F);
+
+/*
+ * Serving: a continuous-batching request loop for many completion solves.
+ * bm_server_create starts a server thread on the current device.  Requests
+ * (bm_server_submit copies the COO data) wait in a FIFO queue and are
+ * admitted while fewer than max_active solves are running and the
+ * device-memory estimate of the request fits mem_budget_gb (0: the whole
+ * device) and the free memory.  Each admitted solve gets its own handle
+ * (bm_create + bm_init with the server's precision) and stays resident
+ * until it finishes.  batched = 1: every cycle runs the BM phases (3
+ * iterations) of all active solves as one bm_batch and then their PG steps
+ * concurrently from `workers` host threads; a solve finishes when the
+ * relative change of F between cycles is below tol or after max_outer
+ * cycles, and requests that arrived meanwhile join at the next cycle.
+ * batched = 0: one solve at a time with bm_solve.
+ */
+typedef struct bm_server_ctx* bm_server;
+typedef struct {
+  int32_t max_active;    /* slots (batched = 0 uses one) */
+  int32_t precision;     /* bm_options.precision of every solve */
+  int32_t batched;       /* 1: batched BM phases + concurrent PG steps; 0: one solve at a time */
+  int32_t workers;       /* host threads for the PG steps */
+  double mem_budget_gb;  /* admission budget (0: device size) */
+  int32_t max_outer;     /* cycles per solve */
+  int32_t pad_;
+  double tol;            /* relative change of F that ends a solve */
+} bm_server_opts;
+typedef struct {
+  int64_t id;            /* from bm_server_submit */
+  int32_t status;        /* bm_status of the solve */
+  int32_t k;             /* final rank */
+  int32_t outer;         /* cycles run */
+  int32_t pad_;
+  double F;              /* final objective */
+  double t_submit;       /* seconds since bm_server_create */
+  double t_start;        /* admission time */
+  double t_done;         /* completion time (latency = t_done - t_submit) */
+} bm_request_result;
+bm_status bm_server_create(const bm_server_opts* o, bm_server* out);
+bm_status bm_server_submit(bm_server s, int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                           const float* vals, double lambda, int32_t k_max, int64_t* id);
+/* Wait until every submitted request has finished (BM_ERR_TIMEOUT after timeout_s > 0). */
+bm_status bm_server_drain(bm_server s, double timeout_s);
+/* Copy up to cap results (completion order); *count receives the number finished. */
+bm_status bm_server_results(bm_server s, bm_request_result* out, int32_t cap, int32_t* count);
+double bm_server_now(bm_server s);
+const char* bm_server_last_error(bm_server s);
+void bm_server_destroy(bm_server s);
+
+/*
  * Distance-geometry (PSD) factorised loss, Eq. "EDM" of the supplement (BM
  * formulation of the kernel-estimation / molecular-conformation QSDP):
  *   g(V) = 1/2 sum_{(i,j) in Omega} w_ij (<E_ij, V V^T> - d_ij^2)^2 + lambda ||V||_F^2

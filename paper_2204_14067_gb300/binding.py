@@ -299,3 +299,100 @@ def bm_loss_grad_csr_noalloc(m, n, row_ptr, col, val, W, H, k, ld, lam, gW, f, s
     if st != BM_OK:
         msg = lib().bm_noalloc_last_error()
         raise BMError(st, msg.decode() if msg else "")
+
+
+_SIGS.update({
+    "bm_batch_create": (_c.c_int, [_P, _c.c_int32, _c.POINTER(_P)]),
+    "bm_batch_destroy": (None, [_P]),
+    "bm_batch_last_error": (_c.c_char_p, [_P]),
+    "bm_batch_bm_phase": (_c.c_int, [_P, _c.c_int32, _P]),
+})
+
+
+def _check_batch(status: int, b=None):
+    if status != BM_OK:
+        msg = lib().bm_batch_last_error(b)
+        raise BMError(status, msg.decode() if msg else "")
+
+
+def bm_batch_create(handles):
+    arr = (_P * len(handles))(*handles)
+    b = _P()
+    _check_batch(lib().bm_batch_create(arr, len(handles), ctypes.byref(b)))
+    return b.value
+
+
+def bm_batch_destroy(b):
+    lib().bm_batch_destroy(b)
+
+
+def bm_batch_bm_phase(b, count, epochs):
+    F = np.zeros(count, np.float64)
+    _check_batch(lib().bm_batch_bm_phase(b, int(epochs), _ptr(F)), b)
+    return F
+
+
+class bm_server_opts(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int32), ("precision", ctypes.c_int32), ("batched", ctypes.c_int32),
+                ("workers", ctypes.c_int32), ("mem_budget_gb", ctypes.c_double), ("max_outer", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class bm_request_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("outer", ctypes.c_int32), ("pad_", ctypes.c_int32), ("F", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+_SIGS.update({
+    "bm_server_create": (_c.c_int, [_c.POINTER(bm_server_opts), _c.POINTER(_P)]),
+    "bm_server_submit": (_c.c_int, [_P, _c.c_int64, _c.c_int64, _c.c_int64, _P, _P, _P, _c.c_double, _c.c_int32,
+                                    _P]),
+    "bm_server_drain": (_c.c_int, [_P, _c.c_double]),
+    "bm_server_results": (_c.c_int, [_P, _P, _c.c_int32, _P]),
+    "bm_server_now": (_c.c_double, [_P]),
+    "bm_server_last_error": (_c.c_char_p, [_P]),
+    "bm_server_destroy": (None, [_P]),
+})
+
+
+def _check_server(status: int, s=None):
+    if status != BM_OK:
+        msg = lib().bm_server_last_error(s)
+        raise BMError(status, msg.decode() if msg else "")
+
+
+def bm_server_create(max_active=16, precision=0, batched=1, workers=8, mem_budget_gb=0.0, max_outer=100,
+                     tol=1e-6):
+    o = bm_server_opts(max_active=max_active, precision=precision, batched=batched, workers=workers,
+                       mem_budget_gb=mem_budget_gb, max_outer=max_outer, tol=tol)
+    s = _P()
+    _check_server(lib().bm_server_create(ctypes.byref(o), ctypes.byref(s)))
+    return s.value
+
+
+def bm_server_submit(s, m, n, rows, cols, vals, lam, k_max):
+    rid = ctypes.c_int64()
+    _check_server(lib().bm_server_submit(s, int(m), int(n), int(rows.shape[0]), _ptr(rows), _ptr(cols), _ptr(vals),
+                                         float(lam), int(k_max), ctypes.byref(rid)), s)
+    return rid.value
+
+
+def bm_server_drain(s, timeout_s=0.0):
+    _check_server(lib().bm_server_drain(s, float(timeout_s)), s)
+
+
+def bm_server_results(s):
+    cnt = ctypes.c_int32()
+    _check_server(lib().bm_server_results(s, None, 0, ctypes.byref(cnt)), s)
+    arr = (bm_request_result * max(1, cnt.value))()
+    _check_server(lib().bm_server_results(s, arr, cnt.value, ctypes.byref(cnt)), s)
+    return [{n: getattr(arr[i], n) for n, _ in bm_request_result._fields_ if n != "pad_"} for i in range(cnt.value)]
+
+
+def bm_server_now(s):
+    return lib().bm_server_now(s)
+
+
+def bm_server_destroy(s):
+    lib().bm_server_destroy(s)

@@ -107,6 +107,7 @@ void copy_in_rows(bm_ctx& h, float* dst, const float* src, int64_t rows, int k) 
 void set_rank(bm_ctx& h, int k) {
   h.k = k;
   h.ld = std::max(4, round_up4(k));
+  h.bf_dirty = true;
 }
 
 // Real roots of c1 + 2 c2 s + 3 c3 s^2 + 4 c4 s^3 = 0; pick the argmin of
@@ -165,17 +166,25 @@ double objective_now(bm_ctx& h, double* f_out = nullptr) {
   return o.f + 0.5 * h.lambda * (o.nW2 + o.nH2);
 }
 
-void bm_phase_dev(bm_ctx& h, int epochs, double* F_out) {
+// `epochs` BM iterations.  Returns F at entry (from the first loss evaluation);
+// *F_out receives F after the last step, read off the line-search quartic
+// (exact in exact arithmetic), so no extra loss pass is spent on it.
+double bm_phase_dev(bm_ctx& h, int epochs, double* F_out) {
   const Index& ix = h.ix;
-  const int64_t mW = ix.m * h.ld, nH = ix.n * h.ld;
-  double F = 0.0;
+  double F = 0.0, F_entry = 0.0;
   double gg_prev = 0.0;
   bool have_prev = false;
+  if (epochs <= 0 || h.k == 0) {
+    F_entry = objective_now(h);
+    if (F_out) *F_out = F_entry;
+    return F_entry;
+  }
   for (int e = 0; e < epochs; ++e) {
+    const int64_t mW = ix.m * h.ld, nH = ix.n * h.ld;
     LossOut o = loss_grad_dev(h, true, true);
     F = o.f + 0.5 * h.lambda * (o.nW2 + o.nH2);
     BM_REQUIRE(std::isfinite(F), BM_ERR_NUMERIC, "bm_bm_phase: objective is not finite");
-    if (h.k == 0) break;
+    if (e == 0) F_entry = F;
     const double gg = dot_dev(h, h.gW.get(), h.gW.get(), mW) + dot_dev(h, h.gH.get(), h.gH.get(), nH);
     double beta = 0.0;
     if (have_prev && gg_prev > 0) {
@@ -203,17 +212,19 @@ void bm_phase_dev(bm_ctx& h, int epochs, double* F_out) {
       axpy_dev(h, h.W.get(), h.DW.get(), (float)s, mW);
       axpy_dev(h, h.H.get(), h.DH.get(), (float)s, nH);
       h.bm_changed = true;
+      h.bf_dirty = true;
       F = poly4(c, s);
     }
-    BM_CUDA(cudaMemcpyAsync(h.gWp.get(), h.gW.get(), mW * sizeof(float), cudaMemcpyDeviceToDevice, h.stream));
-    BM_CUDA(cudaMemcpyAsync(h.gHp.get(), h.gH.get(), nH * sizeof(float), cudaMemcpyDeviceToDevice, h.stream));
+    if (e + 1 < epochs) {
+      BM_CUDA(cudaMemcpyAsync(h.gWp.get(), h.gW.get(), mW * sizeof(float), cudaMemcpyDeviceToDevice, h.stream));
+      BM_CUDA(cudaMemcpyAsync(h.gHp.get(), h.gH.get(), nH * sizeof(float), cudaMemcpyDeviceToDevice, h.stream));
+    }
     gg_prev = gg;
     have_prev = true;
   }
-  if (F_out) {
-    *F_out = objective_now(h);
-  }
+  if (F_out) *F_out = F;
   BM_CUDA(cudaStreamSynchronize(h.stream));
+  return F_entry;
 }
 
 }  // namespace
@@ -262,6 +273,7 @@ bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, cons
     if (opt) o = *opt; else bm_default_options(&o);
     BM_REQUIRE(o.alpha > 0 && std::isfinite(o.alpha), BM_ERR_INVALID, "bm_create: alpha must be > 0");
     BM_REQUIRE(o.lmsvd_p >= 0 && o.lmsvd_p <= 1, BM_ERR_INVALID, "bm_create: lmsvd_p must be 0 or 1");
+    BM_REQUIRE(o.precision == 0 || o.precision == 1, BM_ERR_INVALID, "bm_create: precision must be 0 or 1");
     BM_REQUIRE(o.lmsvd_imax >= 1 && o.k_init >= 1 && o.bm_epochs >= 0 && o.pg_steps >= 0, BM_ERR_INVALID,
                "bm_create: iteration counts out of range");
     h = new bm_ctx();
@@ -287,6 +299,12 @@ bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, cons
     h->r_csr.alloc(std::max<int64_t>(1, nnz));
     h->r_csc.alloc(std::max<int64_t>(1, nnz));
     h->sc.partial.alloc(std::max<int64_t>(1, std::max(ix.rs.nslots, ix.cs.nslots)) * h->ldmax);
+    if (o.precision == 1) {
+      const int64_t ldb = ((h->ldmax + 7) / 8) * 8;
+      h->Wb.alloc(ix.m * ldb);
+      h->Hb.alloc(ix.n * ldb);
+      h->DHb.alloc(ix.n * ldb);
+    }
     h->sc.fseg.alloc(std::max(ix.rs.nseg, ix.cs.nseg) * 4 + 4);
     h->sc.red.alloc(4096);
     h->sc.scal.alloc(64);
@@ -358,6 +376,7 @@ bm_status bm_set_factors(bm_handle h, int32_t k, const float* W, const float* H)
     BM_REQUIRE(k >= 0 && k <= h->k_max, BM_ERR_INVALID, "bm_set_factors: k must be in [0, k_max]");
     BM_REQUIRE(k == 0 || (W && H), BM_ERR_INVALID, "bm_set_factors: NULL factor");
     set_rank(*h, k);
+    h->refine = false;
     const float* Wi = h->ix.transposed ? H : W;
     const float* Hi = h->ix.transposed ? W : H;
     copy_in_rows(*h, h->W.get(), Wi, h->ix.m, k);
@@ -431,20 +450,32 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
       return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     };
     bm_prox_info pi;
-    if (h->k == 0) init_step_dev(*h, &pi);
-    double F_prev = objective_now(*h);
-    double F = F_prev;
+    if (h->k == 0) init_step_dev(*h, nullptr);
+    // F(X_t) is read from the first loss pass of each BM phase; the BM output
+    // X~_t (F from its line search) is an iterate too and may end the solve.
+    double F_prev = 0.0, F = 0.0;
+    bool have_prev = false, ended_on_bm = false;
     int outer = 0;
     for (outer = 1; outer <= so.max_outer; ++outer) {
-      bm_phase_dev(*h, h->opt.bm_epochs, nullptr);
-      for (int x = 0; x < h->opt.pg_steps; ++x) prox_step_dev(*h, h->opt.alpha, &pi);
-      F = objective_now(*h);
+      double F_bm = 0.0;
+      F = bm_phase_dev(*h, h->opt.bm_epochs, &F_bm);
       BM_REQUIRE(std::isfinite(F), BM_ERR_NUMERIC, "bm_solve: objective is not finite");
-      if (so.F_target > 0 && F <= so.F_target) { converged = true; break; }
-      if (std::fabs(F_prev - F) / (1.0 + std::fabs(F_prev)) < so.tol) { converged = true; break; }
+      if (have_prev) {
+        if (so.F_target > 0 && F <= so.F_target) { converged = true; break; }
+        const double rel = std::fabs(F_prev - F) / (1.0 + std::fabs(F_prev));
+        if (rel < so.tol) { converged = true; break; }
+        // BF16 gathers: the final iterations run in FP32 once progress stalls
+        if (h->opt.precision == 1 && !h->refine && rel < 1e-4) h->refine = true;
+      }
+      if (so.F_target > 0 && F_bm <= so.F_target) { converged = true; ended_on_bm = true; break; }
       F_prev = F;
-      if (so.time_limit_s > 0 && elapsed() > so.time_limit_s) break;
+      have_prev = true;
+      for (int x = 0; x < h->opt.pg_steps; ++x) prox_step_dev(*h, h->opt.alpha, nullptr);
+      if (so.time_limit_s > 0 && elapsed() > so.time_limit_s) { ++outer; break; }
     }
+    (void)ended_on_bm;
+    F = objective_now(*h);
+    if (!converged && so.F_target > 0 && F <= so.F_target) converged = true;
     if (info) {
       info->outer = std::min(outer, so.max_outer);
       info->k = h->k;
@@ -452,6 +483,7 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
       info->F = F;
       info->seconds = elapsed();
     }
+    (void)pi;
   });
   if (st == BM_OK && !converged) {
     h->err = "bm_solve: stopped on max_outer or time_limit_s";
@@ -459,6 +491,10 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
   }
   return st;
 }
+
+}  // extern "C" (solve)
+
+extern "C" {
 
 bm_status bm_profile_enable(bm_handle h, int32_t enable) {
   if (!h) return BM_ERR_INVALID;

@@ -29,6 +29,7 @@ struct Index {
   DevBuf<int32_t> col, row;       // CSR column ids, CSC row ids
   DevBuf<float> val, cval;        // A in CSR and in CSC order
   DevBuf<int64_t> csr2csc;        // CSC position of CSR entry e
+  DevBuf<int32_t> csc2csr;        // CSR position of CSC entry q (residual permutation)
   Segs rs, cs;                    // CSR (rows) and CSC (columns) work splits
 };
 
@@ -81,6 +82,13 @@ struct bm_ctx {
   bm::Profiler prof;
   std::string err;
   bool bm_changed = false;       // BM phase moved since the last PG step
+  // BF16 gathers (bm_options.precision == 1): copies of W, H, D_H and of the
+  // SpMM operand, row stride ldb = round_up(ld, 8) elements, zero padded.
+  bool refine = false;           // bm_solve switched to FP32 for the final iterations
+  bool bf_dirty = true;          // W/H changed since the copies were made
+  int ldb = 8;
+  bm::DevBuf<uint16_t> Wb, Hb, DHb, Xb;
+  bool bf_active() const { return opt.precision == 1 && !refine; }
 };
 
 namespace bm {
@@ -107,6 +115,13 @@ struct LossOut {
 // f, gradients (written to h.gW/h.gH when want_grad), residual stored in
 // h.r_csr / h.r_csc when store_r.  Stream-ordered; returns after a sync.
 LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r);
+// BF16 copy of a row-major block (rows x ld floats -> rows x ldb bfloat16, padded with 0)
+void to_bf16_dev(bm_ctx& h, const float* src, int64_t rows, int ld, uint16_t* dst, int ldb);
+// Refresh the BF16 copies of W and H if they are stale.
+void ensure_bf16(bm_ctx& h);
+// Residual r at the current factors in CSR order (CSR pass) and in CSC order
+// (permutation gather); returns f = 1/2 sum r^2.
+double residual_dev(bm_ctx& h);
 // Quartic coefficients c0..c4 of phi(s) along (h.DW, h.DH), using h.r_csr.
 void line_search_coeffs_dev(bm_ctx& h, double c[5]);
 // Dense helpers over m x ld / n x ld arrays (deterministic FP64 reductions).

@@ -370,6 +370,120 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
   if (tid == 0 && sh_state) atomicOr(status, 1);
 }
 
+
+// ---------------------------------------------------------------- parallel Jacobi (FP32)
+// Two-sided cyclic Jacobi with the round-robin ordering: in each round the
+// n/2 disjoint pairs (p, q) are rotated at once (rotation angles from the
+// 2x2 blocks, Golub & Van Loan Sec. 8.5), rows then columns of A and columns
+// of V updated in parallel.  Sweeps stop when every off-diagonal entry is
+// below eps * sqrt(|a_pp a_qq|) or, for null blocks, eps * max|diag|.
+constexpr int kJacMax = 160;
+constexpr int kJacThreads = 512;
+
+__device__ __forceinline__ void rr_pair(int r, int k, int np, int& p, int& q) {
+  // players 0..np-1, player np-1 fixed, others rotate (np even)
+  if (k == 0) {
+    p = np - 1;
+    q = r;
+  } else {
+    p = (r + k) % (np - 1);
+    q = (r - k + (np - 1)) % (np - 1);
+  }
+}
+
+__global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __restrict__ S, int n, int max_sweeps,
+                                                          double* __restrict__ evals, double* __restrict__ evecs,
+                                                          int* __restrict__ status) {
+  extern __shared__ __align__(16) float jac_sm[];
+  const int np = n + (n & 1);           // padded size (even)
+  float* A = jac_sm;                    // np x np
+  float* V = jac_sm + np * np;          // np x np, column j = vector j
+  __shared__ float cs_[kJacMax / 2], sn_[kJacMax / 2];
+  __shared__ int pp_[kJacMax / 2], qq_[kJacMax / 2];
+  __shared__ int sh_rot;
+  __shared__ float sh_floor;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < np * np; idx += nt) {
+    const int i = idx / np, j = idx - i * np;
+    A[idx] = (i < n && j < n) ? (float)(0.5 * (S[i * n + j] + S[j * n + i])) : 0.f;
+    V[idx] = i == j ? 1.f : 0.f;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float fro = 0.f;
+    for (int idx = 0; idx < np * np; ++idx) fro += A[idx] * A[idx];
+    sh_floor = 1e-12f * sqrtf(fro);   // absolute floor for (near) null 2x2 blocks
+  }
+  __syncthreads();
+  const int half = np / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) sh_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      if (tid < half) {
+        int p, q;
+        rr_pair(r, tid, np, p, q);
+        if (p > q) { const int t = p; p = q; q = t; }
+        const float apq = A[p * np + q], app = A[p * np + p], aqq = A[q * np + q];
+        float c = 1.f, s = 0.f;
+        const float thr = fmaxf(1.0e-7f * sqrtf(fabsf(app * aqq)), sh_floor);
+        if (fabsf(apq) > thr && apq != 0.f) {
+          const float th = (aqq - app) / (2.f * apq);
+          const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+          c = rsqrtf(t * t + 1.f);
+          s = t * c;
+          sh_rot = 1;
+        }
+        cs_[tid] = c;
+        sn_[tid] = s;
+        pp_[tid] = p;
+        qq_[tid] = q;
+      }
+      __syncthreads();
+      // rows p, q of A
+      for (int idx = tid; idx < half * np; idx += nt) {
+        const int k = idx / np, col = idx - k * np;
+        const float c = cs_[k], s = sn_[k];
+        if (s == 0.f) continue;
+        const int p = pp_[k], q = qq_[k];
+        const float ap = A[p * np + col], aq = A[q * np + col];
+        A[p * np + col] = c * ap - s * aq;
+        A[q * np + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns p, q of A and V
+      for (int idx = tid; idx < half * np; idx += nt) {
+        const int k = idx / np, row = idx - k * np;
+        const float c = cs_[k], s = sn_[k];
+        if (s == 0.f) continue;
+        const int p = pp_[k], q = qq_[k];
+        const float ap = A[row * np + p], aq = A[row * np + q];
+        A[row * np + p] = c * ap - s * aq;
+        A[row * np + q] = s * ap + c * aq;
+        const float vp = V[row * np + p], vq = V[row * np + q];
+        V[row * np + p] = c * vp - s * vq;
+        V[row * np + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    if (!sh_rot) break;
+  }
+  // sort the first n diagonal entries descending (the padding index stays out)
+  for (int i = tid; i < n; i += nt) {
+    const float di = A[i * np + i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const float dj = A[j * np + j];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    evals[rank] = (double)di;
+    if (!isfinite(di)) atomicOr(status, 2);
+    for (int q = 0; q < n; ++q) evecs[q * n + rank] = (double)V[q * np + i];
+  }
+  if (tid == 0 && sweep >= max_sweeps) atomicOr(status, 4);
+}
+
 // ---------------------------------------------------------------- small helpers
 __global__ void k_select_scale(const double* __restrict__ E, int n, int rows, const int* __restrict__ cols,
                                const double* __restrict__ scale, int ncols, float* __restrict__ T, int ldt) {
@@ -508,11 +622,7 @@ void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, 
   BM_REQUIRE(nb4 <= kGemmThreads, BM_ERR_INVALID, "gemm: too many columns");
   const int rpb = kGemmThreads / nb4;
   const size_t smem = (size_t)a * nb4 * sizeof(float4) + (size_t)rpb * a4 * sizeof(float4);
-  static bool attr = false;
-  if (!attr) {
-    BM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  BM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   BM_REQUIRE(smem <= 200 * 1024, BM_ERR_INVALID, "gemm: block too large");
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A.rows, rpb), (int64_t)num_sms() * 8));
   BM_LAUNCH(h, tag, k_gemm<<<grid, kGemmThreads, smem, h.stream>>>(A.p, A.ld, a, C, ldc, b, Y.p, Y.ld, A.rows,
@@ -541,7 +651,19 @@ void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall&
   a.ld_part = 4 * a.nchunk;
   BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ld_part <= (int64_t)h.sc.partial.n, BM_ERR_INVALID,
              "spmm: partial buffer too small");
-  BM_LAUNCH(h, csr ? "spmm_csr" : "spmm_csc", launch_pipe<1>(a, h.stream));
+  // The residual products of the PG step gather FP32 rows: BF16 operands
+  // leave LmSVD short of its stop tolerance (the factor gathers of the BM
+  // phase are the ones that use BF16).
+  const bool bf = false;
+  if (bf) {
+    const int ldb = ((X.ld + 7) / 8) * 8;
+    BM_REQUIRE((size_t)X.rows * ldb <= h.Xb.n, BM_ERR_INVALID, "spmm: BF16 operand buffer too small");
+    to_bf16_dev(h, X.p, X.rows, X.ld, h.Xb.get(), ldb);
+    a.g0b = h.Xb.get();
+    a.ldb = ldb;
+  }
+  BM_LAUNCH(h, csr ? (bf ? "spmm_csr_bf16" : "spmm_csr") : (bf ? "spmm_csc_bf16" : "spmm_csc"),
+            launch_pipe<1>(a, h.stream, bf));
   if (sg.nmulti) {
     BM_LAUNCH(h, "spmm_fixup",
               k_spmm_fixup<<<grid1(sg.nmulti * X.cols), 256, 0, h.stream>>>(
@@ -552,6 +674,21 @@ void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall&
 
 void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, bool dbl) {
   BM_REQUIRE(n >= 1 && n <= kEigMax, BM_ERR_INVALID, "eigensolver: size out of range");
+  if (!dbl && n <= kJacMax && getenv("BM_EIG_JACOBI")) {
+    // FP32: parallel Jacobi (one block, both matrices in shared memory)
+    const int np = n + (n & 1);
+    const size_t smem = (size_t)2 * np * np * sizeof(float);
+    w.status.alloc(1);
+    BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
+    BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BM_LAUNCH(h, "jacobi_eig_f32",
+              k_jacobi_eig<<<1, kJacThreads, smem, h.stream>>>(S, n, 30, evals, evecs, w.status.get()));
+    int st = 0;
+    BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    BM_CUDA(cudaStreamSynchronize(h.stream));
+    BM_REQUIRE(!(st & 2), BM_ERR_NUMERIC, "eigensolver: non-finite eigenvalue");
+    return;  // (st & 4: sweep cap reached; the FP32 result is still a valid near-diagonalisation)
+  }
   const size_t es = dbl ? 8 : 4;
   const size_t nn = (size_t)n * n * es;
   const size_t cap = 200 * 1024;
@@ -564,21 +701,13 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
   if (!(a_sm && z_sm)) gbuf.alloc(2 * (size_t)kEigMax * kEigMax);
   const size_t smem = (a_sm + z_sm) * nn;
   if (dbl) {
-    static bool attr = false;
-    if (!attr) {
-      BM_CUDA(cudaFuncSetAttribute(k_sym_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
-      attr = true;
-    }
+    BM_CUDA(cudaFuncSetAttribute(k_sym_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
     double* gA = gbuf.get();
     double* gZ = gbuf.get() ? gbuf.get() + (size_t)kEigMax * kEigMax : nullptr;
     BM_LAUNCH(h, "sym_eig_f64", k_sym_eig<double><<<1, kEigThreads, smem, h.stream>>>(
                                     S, n, evals, evecs, gA, gZ, a_sm, z_sm, w.status.get()));
   } else {
-    static bool attr = false;
-    if (!attr) {
-      BM_CUDA(cudaFuncSetAttribute(k_sym_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
-      attr = true;
-    }
+    BM_CUDA(cudaFuncSetAttribute(k_sym_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
     float* gA = reinterpret_cast<float*>(gbuf.get());
     float* gZ = gA ? gA + (size_t)kEigMax * kEigMax : nullptr;
     BM_LAUNCH(h, "sym_eig_f32", k_sym_eig<float><<<1, kEigThreads, smem, h.stream>>>(

@@ -7,6 +7,7 @@
 
 #include "ctx.cuh"
 #include "pipe.cuh"
+#include <cuda_bf16.h>
 
 namespace bm {
 namespace {
@@ -141,8 +142,15 @@ void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
   a.partial = h.sc.partial.get();
   a.ld_part = h.ld;
   a.fseg = fseg;
-  a.r_out = store_r ? (csr ? h.r_csr.get() : h.r_csc.get()) : nullptr;
-  BM_LAUNCH(h, csr ? "grad_csr" : "grad_csc", launch_pipe<0>(a, h.stream));
+  a.r_out = (store_r && csr) ? h.r_csr.get() : nullptr;
+  const bool bf = h.bf_active();
+  if (bf) {
+    ensure_bf16(h);
+    a.g0b = csr ? h.Hb.get() : h.Wb.get();
+    a.ldb = h.ldb;
+  }
+  BM_LAUNCH(h, csr ? (bf ? "grad_csr_bf16" : "grad_csr") : (bf ? "grad_csc_bf16" : "grad_csc"),
+            launch_pipe<0>(a, h.stream, bf));
   if (sg.nmulti) {
     const int64_t work = sg.nmulti * h.ld;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), num_sms() * 8));
@@ -191,12 +199,59 @@ LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r) {
   run_pass(h, true, store_r, fseg);
   k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, ix.rs.nseg, 1, 0, h.sc.scal.get() + 1);
   BM_CHECK_LAUNCH();
-  if (want_grad || store_r) run_pass(h, false, store_r, nullptr);
+  if (want_grad) run_pass(h, false, false, nullptr);
   BM_CUDA(cudaMemcpyAsync(&o.f, h.sc.scal.get() + 1, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
   BM_CUDA(cudaStreamSynchronize(h.stream));
   o.nW2 = dot_dev(h, h.W.get(), h.W.get(), ix.m * h.ld);
   o.nH2 = dot_dev(h, h.H.get(), h.H.get(), ix.n * h.ld);
   return o;
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, int64_t rows, int ld, uint16_t* __restrict__ dst, int ldb) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rows * ldb;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / ldb;
+    const int c = (int)(t - r * ldb);
+    const float x = c < ld ? src[r * ld + c] : 0.f;
+    dst[t] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+  }
+}
+
+__global__ void k_permute(const float* __restrict__ src, const int32_t* __restrict__ map, float* __restrict__ dst,
+                          int64_t n) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    dst[q] = __ldg(src + __ldg(map + q));
+}
+
+void to_bf16_dev(bm_ctx& h, const float* src, int64_t rows, int ld, uint16_t* dst, int ldb) {
+  if (rows == 0) return;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * ldb, 256), (int64_t)num_sms() * 16));
+  BM_LAUNCH(h, "to_bf16", k_to_bf16<<<grid, 256, 0, h.stream>>>(src, rows, ld, dst, ldb));
+}
+
+void ensure_bf16(bm_ctx& h) {
+  if (!h.bf_active() || !h.bf_dirty) return;
+  h.ldb = ((h.ld + 7) / 8) * 8;
+  to_bf16_dev(h, h.W.get(), h.ix.m, h.ld, h.Wb.get(), h.ldb);
+  to_bf16_dev(h, h.H.get(), h.ix.n, h.ld, h.Hb.get(), h.ldb);
+  h.bf_dirty = false;
+}
+
+double residual_dev(bm_ctx& h) {
+  const Index& ix = h.ix;
+  double* fseg = h.sc.fseg.get();
+  run_pass(h, true, true, fseg);
+  k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, ix.rs.nseg, 1, 0, h.sc.scal.get() + 1);
+  BM_CHECK_LAUNCH();
+  if (ix.nnz) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix.nnz, 256), (int64_t)num_sms() * 16));
+    BM_LAUNCH(h, "permute_r", k_permute<<<grid, 256, 0, h.stream>>>(h.r_csr.get(), ix.csc2csr.get(), h.r_csc.get(),
+                                                                   ix.nnz));
+  }
+  double f = 0;
+  BM_CUDA(cudaMemcpyAsync(&f, h.sc.scal.get() + 1, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+  BM_CUDA(cudaStreamSynchronize(h.stream));
+  return f;
 }
 
 void line_search_coeffs_dev(bm_ctx& h, double c[5]) {
@@ -216,7 +271,15 @@ void line_search_coeffs_dev(bm_ctx& h, double c[5]) {
   a.ld = h.ld;
   a.nchunk = h.ld / 4;
   a.fseg = h.sc.fseg.get();
-  BM_LAUNCH(h, "linesearch_csr", launch_pipe<2>(a, h.stream));
+  const bool bf = h.bf_active();
+  if (bf) {
+    ensure_bf16(h);
+    to_bf16_dev(h, h.DH.get(), ix.n, h.ld, h.DHb.get(), h.ldb);
+    a.g0b = h.Hb.get();
+    a.g1b = h.DHb.get();
+    a.ldb = h.ldb;
+  }
+  BM_LAUNCH(h, bf ? "linesearch_csr_bf16" : "linesearch_csr", launch_pipe<2>(a, h.stream, bf));
   for (int q = 0; q < 4; ++q) {
     k_sum_double<<<1, 1024, 0, h.stream>>>(a.fseg, ix.rs.nseg, 4, q, h.sc.scal.get() + 2 + q);
     BM_CHECK_LAUNCH();

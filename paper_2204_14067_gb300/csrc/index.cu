@@ -264,7 +264,7 @@ __global__ void k_csr_finalize(const uint64_t* __restrict__ sk, const uint32_t* 
 __global__ void k_csc_finalize(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
                                const float* __restrict__ val, int64_t nnz, uint64_t mint,
                                int32_t* __restrict__ row, float* __restrict__ cval,
-                               int64_t* __restrict__ csr2csc) {
+                               int64_t* __restrict__ csr2csc, int32_t* __restrict__ csc2csr) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz;
        q += (int64_t)gridDim.x * blockDim.x) {
     uint64_t key = sk[q];
@@ -273,6 +273,7 @@ __global__ void k_csc_finalize(const uint64_t* __restrict__ sk, const uint32_t* 
     uint32_t e = sv[q];
     cval[q] = val[e];
     csr2csc[e] = q;
+    csc2csr[q] = (int32_t)e;
   }
 }
 
@@ -377,6 +378,7 @@ void build_index(bm_ctx& h, int64_t m, int64_t n, int64_t nnz, const int32_t* ro
   ix.val.alloc(nnz);
   ix.cval.alloc(nnz);
   ix.csr2csc.alloc(nnz);
+  ix.csc2csr.alloc(nnz);
   {
     DevBuf<uint64_t> k0, k1;
     DevBuf<uint32_t> v0, v1;
@@ -406,7 +408,8 @@ void build_index(bm_ctx& h, int64_t m, int64_t n, int64_t nnz, const int32_t* ro
     BM_CHECK_LAUNCH();
     if (nnz > 0) {
       k_csc_finalize<<<grid_for(nnz, 256), 256, 0, st>>>(k1.get(), v1.get(), ix.val.get(), nnz, M,
-                                                         ix.row.get(), ix.cval.get(), ix.csr2csc.get());
+                                                         ix.row.get(), ix.cval.get(), ix.csr2csc.get(),
+                                                         ix.csc2csr.get());
       BM_CHECK_LAUNCH();
     }
     BM_CUDA(cudaStreamSynchronize(st));

@@ -53,7 +53,24 @@ struct PipeArgs {
   int ld_part;
   double* fseg;           // MODE 0: per-segment 1/2 sum r^2 (nullable); MODE 2: 4 sums per segment
   float* r_out;           // MODE 0: residual in pass order (nullable)
+  const void* g0b;        // BF16 copies of g0 / g1 (row stride ldb elements, ldb % 8 == 0,
+  const void* g1b;        //   zero padded) used instead of g0 / g1 when gathering in BF16
+  int ldb;
 };
+
+__device__ __forceinline__ float bf16lo(unsigned u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16hi(unsigned u) { return __uint_as_float(u & 0xffff0000u); }
+
+// chunk c (4 values) of a staged row: FP32 rows hold 4 floats per chunk, BF16
+// rows 4 bfloat16 (8 bytes) per chunk
+template <bool BF>
+__device__ __forceinline__ float4 stage4(const float* slot, int c) {
+  if (BF) {
+    const uint2 u = *reinterpret_cast<const uint2*>(slot + 2 * c);
+    return make_float4(bf16lo(u.x), bf16hi(u.x), bf16lo(u.y), bf16hi(u.y));
+  }
+  return *reinterpret_cast<const float4*>(slot + 4 * c);
+}
 
 __device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -76,18 +93,20 @@ struct PipeShape {
 
 // floats of one stage: BATCH entries x NG slots + NO owned slots (each 4*nchunk + 4
 // floats; the pad spreads the slots over the banks), + BATCH scalars
-__host__ __device__ inline int pipe_stage_floats(int mode, int nchunk) {
+__host__ __device__ inline int pipe_stage_floats(int mode, int nchunk, bool bf) {
   const int ng = mode == 2 ? 2 : 1;
   const int no = mode == 1 ? 0 : (mode == 2 ? 2 : 1);
   const int batch = mode == 2 ? (BM_PIPE_BATCH > 8 ? BM_PIPE_BATCH / 2 : 8) : BM_PIPE_BATCH;
-  return (batch * ng + no) * (4 * nchunk + 4) + batch;
+  const int sl_g = bf ? ((2 * nchunk + 4 + 3) & ~3) : 4 * nchunk + 4;  // gathered slot (floats, 16-B multiple)
+  const int sl_o = 4 * nchunk + 4;                        // owned slot (FP32)
+  return batch * ng * sl_g + no * sl_o + batch;
 }
 
-inline size_t pipe_smem_bytes(int mode, int nchunk) {
-  return (size_t)kPipeWarps * BM_PIPE_STAGES * pipe_stage_floats(mode, nchunk) * sizeof(float);
+inline size_t pipe_smem_bytes(int mode, int nchunk, bool bf) {
+  return (size_t)kPipeWarps * BM_PIPE_STAGES * pipe_stage_floats(mode, nchunk, bf) * sizeof(float);
 }
 
-template <int MODE, int V>
+template <int MODE, int V, bool BF>
 __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int NG = PipeShape<MODE>::NG, NO = PipeShape<MODE>::NO, S = PipeShape<MODE>::S;
@@ -95,36 +114,86 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
   extern __shared__ __align__(16) float pipe_sm[];
   const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
   const int nch = a.nchunk;
-  const int SL = 4 * nch + 4;
-  const int SF = (BATCH * NG + NO) * SL + BATCH;
+  const int SL = BF ? ((2 * nch + 4 + 3) & ~3) : 4 * nch + 4;   // gathered slot (floats, 16-B multiple)
+  const int SO = 4 * nch + 4;                       // owned slot (floats)
+  const int SF = BATCH * NG * SL + NO * SO + BATCH;
+  const int OWN = BATCH * NG * SL;                  // offset of the owned slots
+  const int SCL = OWN + NO * SO;                    // offset of the scalars
   float* ring = pipe_sm + (size_t)(threadIdx.x >> 5) * S * SF;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
 
-  // issue cursor (segment bounds cached in registers)
+  // Issue cursor.  The indices and scalars of the next batch to issue are
+  // loaded one iteration ahead (j_pf, s_pf), so the cp.async source addresses
+  // never wait on a just-issued load.
   int64_t is = warp0, ib = 0, i_beg = 0, i_end = 0, i_nb = 0;
   int i_row = 0;
-  if (is < a.nseg) {
-    i_beg = a.seg_beg[is];
-    i_end = a.seg_end[is];
-    i_nb = max((int64_t)1, (i_end - i_beg + BATCH - 1) / BATCH);
-    i_row = a.seg_row[is];
-  }
+  int j_pf = 0;
+  float s_pf = 0.f;
+  auto load_seg = [&]() {
+    if (is < a.nseg) {
+      i_beg = a.seg_beg[is];
+      i_end = a.seg_end[is];
+      i_nb = max((int64_t)1, (i_end - i_beg + BATCH - 1) / BATCH);
+      i_row = a.seg_row[is];
+    }
+  };
+  auto prefetch = [&]() {
+    if (is < a.nseg && lane < BATCH) {
+      const int64_t e = i_beg + (int64_t)BATCH * ib + lane;
+      const bool v = e < i_end;
+      j_pf = v ? __ldg(a.idx + e) : 0;
+      s_pf = v ? __ldg(a.scal + e) : 0.f;
+    }
+  };
+  load_seg();
+  prefetch();
   auto issue = [&](int stage) {
     if (is < a.nseg) {
       float* st = ring + stage * SF;
       const int64_t e0 = i_beg + (int64_t)BATCH * ib;
       const int cnt = (int)min((int64_t)BATCH, i_end - e0);
-      if (lane < BATCH) {
+      if (lane < BATCH) st[SCL + lane] = s_pf;
+      if (!BF) {
+        // consecutive lanes copy consecutive 16-byte chunks of a row (coalesced)
+        int ent = lane / nch, c = lane - ent * nch;
+        const int q32 = 32 / nch, r32 = 32 - q32 * nch;
+        const int total = BATCH * nch;
+        for (int u0 = 0; u0 < total; u0 += 32) {   // uniform trip count across the warp
+          const int jj = __shfl_sync(FULL, j_pf, ent & 31);
+          if (u0 + lane < total) {
+            const bool v = ent < cnt;
+            float* d0 = st + ent * NG * SL;
+            cp_async16(d0 + 4 * c, a.g0 + (int64_t)jj * a.ld + 4 * c, v);
+            if (NG == 2) cp_async16(d0 + SL + 4 * c, a.g1 + (int64_t)jj * a.ld + 4 * c, v);
+          }
+          ent += q32;
+          c += r32;
+          if (c >= nch) {
+            c -= nch;
+            ++ent;
+          }
+        }
+      } else if (lane < BATCH) {
         const bool v = lane < cnt;
-        const int j = v ? __ldg(a.idx + e0 + lane) : 0;
-        st[(BATCH * NG + NO) * SL + lane] = v ? __ldg(a.scal + e0 + lane) : 0.f;
-        const float* s0 = a.g0 + (int64_t)j * a.ld;
         float* d0 = st + lane * NG * SL;
-        for (int c = 0; c < nch; ++c) cp_async16(d0 + 4 * c, s0 + 4 * c, v);
-        if (NG == 2) {
-          const float* s1 = a.g1 + (int64_t)j * a.ld;
-          for (int c = 0; c < nch; ++c) cp_async16(d0 + SL + 4 * c, s1 + 4 * c, v);
+        if (BF) {
+          const int nc16 = (nch + 1) >> 1;   // 16-byte pieces of 4*nch bfloat16
+          const float* s0 = reinterpret_cast<const float*>(
+              reinterpret_cast<const unsigned short*>(a.g0b) + (int64_t)j_pf * a.ldb);
+          for (int c = 0; c < nc16; ++c) cp_async16(d0 + 4 * c, s0 + 4 * c, v);
+          if (NG == 2) {
+            const float* s1 = reinterpret_cast<const float*>(
+                reinterpret_cast<const unsigned short*>(a.g1b) + (int64_t)j_pf * a.ldb);
+            for (int c = 0; c < nc16; ++c) cp_async16(d0 + SL + 4 * c, s1 + 4 * c, v);
+          }
+        } else {
+          const float* s0 = a.g0 + (int64_t)j_pf * a.ld;
+          for (int c = 0; c < nch; ++c) cp_async16(d0 + 4 * c, s0 + 4 * c, v);
+          if (NG == 2) {
+            const float* s1 = a.g1 + (int64_t)j_pf * a.ld;
+            for (int c = 0; c < nch; ++c) cp_async16(d0 + SL + 4 * c, s1 + 4 * c, v);
+          }
         }
       }
       if (NO > 0 && ib == 0) {
@@ -132,19 +201,15 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
           const int oi = NO == 2 ? (u >= nch ? 1 : 0) : 0;
           const int c = u - oi * nch;
           const float* src = (oi == 0 ? a.o0 : a.o1) + (int64_t)i_row * a.ld + 4 * c;
-          cp_async16(st + (BATCH * NG + oi) * SL + 4 * c, src, true);
+          cp_async16(st + OWN + oi * SO + 4 * c, src, true);
         }
       }
       if (++ib >= i_nb) {
         ib = 0;
         is += nwarps;
-        if (is < a.nseg) {
-          i_beg = a.seg_beg[is];
-          i_end = a.seg_end[is];
-          i_nb = max((int64_t)1, (i_end - i_beg + BATCH - 1) / BATCH);
-          i_row = a.seg_row[is];
-        }
+        load_seg();
       }
+      prefetch();
     }
     cp_async_commit();
   };
@@ -178,9 +243,9 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const int c = l + 4 * v;
-        if (NO >= 1) w[v] = c < nch ? *reinterpret_cast<const float4*>(st + BATCH * NG * SL + 4 * c)
+        if (NO >= 1) w[v] = c < nch ? *reinterpret_cast<const float4*>(st + OWN + 4 * c)
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (NO == 2) dw[v] = c < nch ? *reinterpret_cast<const float4*>(st + (BATCH * NG + 1) * SL + 4 * c)
+        if (NO == 2) dw[v] = c < nch ? *reinterpret_cast<const float4*>(st + OWN + SO + 4 * c)
                                      : make_float4(0.f, 0.f, 0.f, 0.f);
         acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -190,7 +255,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
     for (int t = 0; t < ROUNDS; ++t) {
       const int ent = t * 8 + g;
       const bool ok = ent < cnt;
-      const float sc = st[(BATCH * NG + NO) * SL + ent];
+      const float sc = st[SCL + ent];
       const float* r0 = st + (ent * NG) * SL;
       if (MODE == 0) {
         float4 hv[V];
@@ -198,7 +263,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int c = l + 4 * v;
-          hv[v] = c < nch ? *reinterpret_cast<const float4*>(r0 + 4 * c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          hv[v] = c < nch ? stage4<BF>(r0, c) : make_float4(0.f, 0.f, 0.f, 0.f);
           d = fmaf(w[v].x, hv[v].x, fmaf(w[v].y, hv[v].y, fmaf(w[v].z, hv[v].z, fmaf(w[v].w, hv[v].w, d))));
         }
         d += __shfl_xor_sync(FULL, d, 1);
@@ -221,7 +286,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
         for (int v = 0; v < V; ++v) {
           const int c = l + 4 * v;
           if (c < nch) {
-            const float4 x = *reinterpret_cast<const float4*>(r0 + 4 * c);
+            const float4 x = stage4<BF>(r0, c);
             acc[v].x = fmaf(vv, x.x, acc[v].x);
             acc[v].y = fmaf(vv, x.y, acc[v].y);
             acc[v].z = fmaf(vv, x.z, acc[v].z);
@@ -235,8 +300,8 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
         for (int v = 0; v < V; ++v) {
           const int c = l + 4 * v;
           if (c < nch) {
-            const float4 h = *reinterpret_cast<const float4*>(r0 + 4 * c);
-            const float4 dh = *reinterpret_cast<const float4*>(r1 + 4 * c);
+            const float4 h = stage4<BF>(r0, c);
+            const float4 dh = stage4<BF>(r1, c);
             b = fmaf(dw[v].x, h.x, fmaf(dw[v].y, h.y, fmaf(dw[v].z, h.z, fmaf(dw[v].w, h.w, b))));
             b = fmaf(w[v].x, dh.x, fmaf(w[v].y, dh.y, fmaf(w[v].z, dh.z, fmaf(w[v].w, dh.w, b))));
             c2 = fmaf(dw[v].x, dh.x, fmaf(dw[v].y, dh.y, fmaf(dw[v].z, dh.z, fmaf(dw[v].w, dh.w, c2))));
@@ -333,25 +398,284 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
   cp_async_wait<0>();
 }
 
-// Launch k_pipe<MODE, V> with V = ceil(nchunk / 4) (<= 8).
+
+// ----------------------------------------------------------------------------
+// Direct variant (no shared-memory staging): one warp per segment, eight
+// entries per step, four lanes per entry loading V float4 chunks of the
+// gathered row straight into registers (64 contiguous bytes per lane group),
+// two steps unrolled.  Same arguments and results as k_pipe.
+// ----------------------------------------------------------------------------
+template <bool BF>
+__device__ __forceinline__ float4 gather4(const float* g, const void* gb, int64_t j, int ld, int ldb, int c) {
+  if (BF) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(gb) + j * ldb) + c);
+    return make_float4(bf16lo(u.x), bf16hi(u.x), bf16lo(u.y), bf16hi(u.y));
+  }
+  return __ldg(reinterpret_cast<const float4*>(g + j * ld) + c);
+}
+
+// One segment s of a pass (the warp's lanes cooperate).
+template <int MODE, int V, bool BF>
+__device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
+  const int nch = a.nchunk;
+  const int i = a.seg_row[s];
+  const int64_t beg = a.seg_beg[s], end = a.seg_end[s];
+  float4 w[V], dw[V], acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int c = l + 4 * v;
+    const bool in = c < nch;
+    w[v] = (MODE != 1 && in) ? __ldg(reinterpret_cast<const float4*>(a.o0 + (int64_t)i * a.ld) + c)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    dw[v] = (MODE == 2 && in) ? __ldg(reinterpret_cast<const float4*>(a.o1 + (int64_t)i * a.ld) + c)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float fs = 0.f, s_rb = 0.f, s_bb = 0.f, s_bc = 0.f, s_cc = 0.f;
+  for (int64_t e0 = beg; e0 < end; e0 += 32) {
+    const int64_t e = e0 + lane;
+    const bool valid = e < end;
+    const int j = valid ? __ldg(a.idx + e) : 0;
+    const float sv = valid ? __ldg(a.scal + e) : 0.f;
+#pragma unroll 2
+    for (int t = 0; t < 4; ++t) {
+      const int src = t * 8 + g;
+      const int64_t jj = __shfl_sync(FULL, j, src);
+      const float sc = __shfl_sync(FULL, sv, src);
+      const bool ok = e0 + src < end;
+      if (MODE == 0) {
+        float4 hv[V];
+        float d = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int c = l + 4 * v;
+          hv[v] = c < nch ? gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          d = fmaf(w[v].x, hv[v].x, fmaf(w[v].y, hv[v].y, fmaf(w[v].z, hv[v].z, fmaf(w[v].w, hv[v].w, d))));
+        }
+        d += __shfl_xor_sync(FULL, d, 1);
+        d += __shfl_xor_sync(FULL, d, 2);
+        const float r = ok ? d - sc : 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          acc[v].x = fmaf(r, hv[v].x, acc[v].x);
+          acc[v].y = fmaf(r, hv[v].y, acc[v].y);
+          acc[v].z = fmaf(r, hv[v].z, acc[v].z);
+          acc[v].w = fmaf(r, hv[v].w, acc[v].w);
+        }
+        if (l == 0) {
+          fs = fmaf(r, r, fs);
+          if (a.r_out && ok) a.r_out[e0 + src] = r;
+        }
+      } else if (MODE == 1) {
+        const float vv = ok ? sc : 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int c = l + 4 * v;
+          if (c < nch) {
+            const float4 x = gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c);
+            acc[v].x = fmaf(vv, x.x, acc[v].x);
+            acc[v].y = fmaf(vv, x.y, acc[v].y);
+            acc[v].z = fmaf(vv, x.z, acc[v].z);
+            acc[v].w = fmaf(vv, x.w, acc[v].w);
+          }
+        }
+      } else {
+        float b = 0.f, c2 = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int c = l + 4 * v;
+          if (c < nch) {
+            const float4 h = gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c);
+            const float4 dh = gather4<BF>(a.g1, a.g1b, jj, a.ld, a.ldb, c);
+            b = fmaf(dw[v].x, h.x, fmaf(dw[v].y, h.y, fmaf(dw[v].z, h.z, fmaf(dw[v].w, h.w, b))));
+            b = fmaf(w[v].x, dh.x, fmaf(w[v].y, dh.y, fmaf(w[v].z, dh.z, fmaf(w[v].w, dh.w, b))));
+            c2 = fmaf(dw[v].x, dh.x, fmaf(dw[v].y, dh.y, fmaf(dw[v].z, dh.z, fmaf(dw[v].w, dh.w, c2))));
+          }
+        }
+        b += __shfl_xor_sync(FULL, b, 1);
+        b += __shfl_xor_sync(FULL, b, 2);
+        c2 += __shfl_xor_sync(FULL, c2, 1);
+        c2 += __shfl_xor_sync(FULL, c2, 2);
+        if (ok && l == 0) {
+          s_rb = fmaf(sc, b, s_rb);
+          s_bb = fmaf(b, b, fmaf(2.f * sc, c2, s_bb));
+          s_bc = fmaf(b, c2, s_bc);
+          s_cc = fmaf(c2, c2, s_cc);
+        }
+      }
+    }
+  }
+  if (MODE != 2) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+#pragma unroll
+      for (int mk = 4; mk < 32; mk <<= 1) {
+        acc[v].x += __shfl_xor_sync(FULL, acc[v].x, mk);
+        acc[v].y += __shfl_xor_sync(FULL, acc[v].y, mk);
+        acc[v].z += __shfl_xor_sync(FULL, acc[v].z, mk);
+        acc[v].w += __shfl_xor_sync(FULL, acc[v].w, mk);
+      }
+    }
+    if (g == 0) {
+      const int slot = a.seg_slot[s];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int c = l + 4 * v;
+        if (c < nch) {
+          if (slot < 0) {
+            float4* op = reinterpret_cast<float4*>(a.out + (int64_t)i * a.ld_out + 4 * c);
+            float4 o;
+            if (MODE == 0) {
+              o = acc[v];
+              o.x = fmaf(a.lam, w[v].x, o.x);
+              o.y = fmaf(a.lam, w[v].y, o.y);
+              o.z = fmaf(a.lam, w[v].z, o.z);
+              o.w = fmaf(a.lam, w[v].w, o.w);
+            } else {
+              o = *op;
+              o.x = fmaf(a.gamma, acc[v].x, o.x);
+              o.y = fmaf(a.gamma, acc[v].y, o.y);
+              o.z = fmaf(a.gamma, acc[v].z, o.z);
+              o.w = fmaf(a.gamma, acc[v].w, o.w);
+            }
+            *op = o;
+          } else {
+            *reinterpret_cast<float4*>(a.partial + (int64_t)slot * a.ld_part + 4 * c) = acc[v];
+          }
+        }
+      }
+    }
+    if (MODE == 0 && a.fseg) {
+#pragma unroll
+      for (int mk = 16; mk > 0; mk >>= 1) fs += __shfl_xor_sync(FULL, fs, mk);
+      if (lane == 0) a.fseg[s] = 0.5 * (double)fs;
+    }
+  } else {
+#pragma unroll
+    for (int mk = 16; mk > 0; mk >>= 1) {
+      s_rb += __shfl_xor_sync(FULL, s_rb, mk);
+      s_bb += __shfl_xor_sync(FULL, s_bb, mk);
+      s_bc += __shfl_xor_sync(FULL, s_bc, mk);
+      s_cc += __shfl_xor_sync(FULL, s_cc, mk);
+    }
+    if (lane == 0) {
+      a.fseg[s * 4 + 0] = s_rb;
+      a.fseg[s * 4 + 1] = s_bb;
+      a.fseg[s * 4 + 2] = s_bc;
+      a.fseg[s * 4 + 3] = s_cc;
+    }
+  }
+}
+
+template <int MODE, int V, bool BF>
+__global__ void __launch_bounds__(256, 3) k_direct(PipeArgs a) {
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < a.nseg; s += nwarps)
+    direct_segment<MODE, V, BF>(a, s);
+}
+
+// The same pass over several problems in one launch: segment sg of the
+// concatenated segment lists belongs to problem p with
+// prefix[p] <= sg < prefix[p + 1].
+template <int MODE, int V, bool BF>
+__global__ void __launch_bounds__(256, 3) k_direct_batch(const PipeArgs* __restrict__ args,
+                                                         const int64_t* __restrict__ prefix, int count) {
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = prefix[count];
+  for (int64_t sg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sg < total; sg += nwarps) {
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (prefix[mid] <= sg) lo = mid; else hi = mid;
+    }
+    direct_segment<MODE, V, BF>(args[lo], sg - prefix[lo]);
+  }
+}
+
+// Launch k_direct_batch for problems with the same chunk count; total_segs =
+// prefix[count] (host copy) sizes the grid.
 template <int MODE>
-void launch_pipe(const PipeArgs& a, cudaStream_t st) {
+void launch_direct_batch(const PipeArgs* args_d, const int64_t* prefix_d, int count, int64_t total_segs,
+                         int nchunk, bool bf, cudaStream_t st) {
+  const int V = (nchunk + 3) / 4;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(total_segs, 1), 8),
+                                                               (int64_t)num_sms() * 24));
+#define BM_DBATCH_CASE(VV)                                                                   \
+  case VV:                                                                                   \
+    if (bf) k_direct_batch<MODE, VV, true><<<grid, 256, 0, st>>>(args_d, prefix_d, count);   \
+    else k_direct_batch<MODE, VV, false><<<grid, 256, 0, st>>>(args_d, prefix_d, count);     \
+    break;
+  switch (V) {
+    BM_DBATCH_CASE(1)
+    BM_DBATCH_CASE(2)
+    BM_DBATCH_CASE(3)
+    BM_DBATCH_CASE(4)
+    BM_DBATCH_CASE(5)
+    BM_DBATCH_CASE(6)
+    BM_DBATCH_CASE(7)
+    BM_DBATCH_CASE(8)
+    default:
+      throw Error{BM_ERR_INVALID, "batched pass: more than 128 columns"};
+  }
+#undef BM_DBATCH_CASE
+}
+
+// Kernel selection: BM_SPARSE_KERNEL=pipe|direct (default direct).
+inline bool use_pipe_kernel() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("BM_SPARSE_KERNEL");
+    v = (e && e[0] == 'p') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// Launch k_pipe<MODE, V, BF> with V = ceil(nchunk / 4) (<= 8); BF selects the
+// BF16 copies (a.g0b, a.g1b) for the gathered rows.
+template <int MODE>
+void launch_pipe(const PipeArgs& a, cudaStream_t st, bool bf = false) {
   const int V = (a.nchunk + 3) / 4;
-  const size_t smem = pipe_smem_bytes(MODE, a.nchunk);
+  if (!use_pipe_kernel()) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(a.nseg, 1), 8),
+                                                                 (int64_t)num_sms() * 24));
+#define BM_DIRECT_CASE(VV)                                                  \
+  case VV:                                                                  \
+    if (bf) k_direct<MODE, VV, true><<<grid, 256, 0, st>>>(a);              \
+    else k_direct<MODE, VV, false><<<grid, 256, 0, st>>>(a);                \
+    return;
+    switch (V) {
+      BM_DIRECT_CASE(1)
+      BM_DIRECT_CASE(2)
+      BM_DIRECT_CASE(3)
+      BM_DIRECT_CASE(4)
+      BM_DIRECT_CASE(5)
+      BM_DIRECT_CASE(6)
+      BM_DIRECT_CASE(7)
+      BM_DIRECT_CASE(8)
+      default:
+        throw Error{BM_ERR_INVALID, "sparse pass: more than 128 columns"};
+    }
+#undef BM_DIRECT_CASE
+  }
+  const size_t smem = pipe_smem_bytes(MODE, a.nchunk, bf);
   const int warps = kPipeWarps;
   const int blocks_per_sm = (int)std::max<size_t>(1, (200 * 1024) / std::max<size_t>(smem, 1));
   const int64_t need = ceil_div(std::max<int64_t>(a.nseg, 1), warps);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * blocks_per_sm));
-#define BM_PIPE_CASE(VV)                                                                          \
-  case VV: {                                                                                      \
-    static bool attr = false;                                                                     \
-    if (!attr) {                                                                                  \
-      BM_CUDA(cudaFuncSetAttribute(k_pipe<MODE, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                   200 * 1024));                                                  \
-      attr = true;                                                                                \
-    }                                                                                             \
-    k_pipe<MODE, VV><<<grid, warps * 32, smem, st>>>(a);                                          \
-    break;                                                                                        \
+#define BM_PIPE_CASE(VV)                                                                               \
+  case VV: {                                                                                           \
+    if (bf) {                                                                                          \
+      BM_CUDA(cudaFuncSetAttribute(k_pipe<MODE, VV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                   (int)smem));                                                        \
+      k_pipe<MODE, VV, true><<<grid, warps * 32, smem, st>>>(a);                                       \
+    } else {                                                                                           \
+      BM_CUDA(cudaFuncSetAttribute(k_pipe<MODE, VV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                   (int)smem));                                                        \
+      k_pipe<MODE, VV, false><<<grid, warps * 32, smem, st>>>(a);                                      \
+    }                                                                                                  \
+    break;                                                                                             \
   }
   switch (V) {
     BM_PIPE_CASE(1)

@@ -388,6 +388,7 @@ void prox_create(bm_ctx& h) {
   ps.ldq2 = round_up4(2 * ps.qcap);
   for (auto& b : ps.mbuf) b.alloc((size_t)h.ix.m * ps.ldq2);
   ps.Y.alloc((size_t)h.ix.n * ps.ldq);
+
   ps.Bt.alloc((size_t)h.ix.n * ps.ldq);
   const size_t q2 = (size_t)2 * ps.qcap;
   ps.G.alloc(q2 * q2);
@@ -431,7 +432,7 @@ void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info) {
   const int m = (int)h.ix.m;
   (void)m;
   // R at X~ in both orders
-  loss_grad_dev(h, true, true);
+  residual_dev(h);
   const double frob2 = frob2_dev(h, alpha);
   if (!ps.initialized) {
     // U_t := orth(W) (factors set by the caller)

@@ -12,4 +12,5 @@ from .gen import (  # noqa: F401
     random_factors,
     PairProblem,
     self_avoiding_chain,
+    serving_requests,
 )

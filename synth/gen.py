@@ -327,3 +327,36 @@ def self_avoiding_chain(n=30_000, cutoff=6.0, noise=0.10, exclusion=1.0, seed=3,
     return PairProblem(name, n, pairs[:, 0].astype(np.int32), pairs[:, 1].astype(np.int32), d.astype(np.float32),
                        X, seed, f"3-D self-avoiding walk, unit bonds, exclusion {exclusion}, pairs within {cutoff}, "
                                 f"d = true*(1+U(-{noise},{noise}))")
+
+
+def serving_requests(count=2000, seed=4, m_range=(1_000, 200_000), n_range=(500, 20_000),
+                     density_range=(0.001, 0.02), rank_range=(2, 16), lam_grid=(0.02, 0.05, 0.1, 0.2, 0.5),
+                     rate=None, k_max=32, max_nnz=None):
+    """A stream of completion requests: m, n and the density log-uniform in
+    their ranges, nnz = density*m*n (capped at max_nnz), planted rank uniform
+    in rank_range, ratings as in the recommendation workload, lambda = a grid
+    value times max|A|; arrival times from a Poisson process of the given
+    rate (requests per second; None: all at 0).  Returns (problems, arrivals)."""
+    rng = _rng(seed, 5)
+    lu = lambda lo, hi, size: np.exp(rng.uniform(np.log(lo), np.log(hi), size))
+    ms = np.round(lu(*m_range, count)).astype(np.int64)
+    ns = np.round(lu(*n_range, count)).astype(np.int64)
+    ds = lu(*density_range, count)
+    ranks = rng.integers(rank_range[0], rank_range[1] + 1, count)
+    lams = rng.choice(np.asarray(lam_grid), count)
+    probs = []
+    for t in range(count):
+        m, n = int(ms[t]), int(ns[t])
+        nnz = int(round(ds[t] * m * n))
+        if max_nnz is not None:
+            nnz = min(nnz, max_nnz)
+        nnz = max(nnz, max(m, n))
+        nnz = min(nnz, m * (n // 2))
+        p = zipf_ratings(m, n, nnz, rank=int(ranks[t]), mean=3.6, sd=1.0, lo=1, hi=5, seed=seed * 100003 + t,
+                         lam_frac=float(lams[t]), k_max=min(k_max, m, n), name=f"req{t}", shuffle=True)
+        probs.append(p)
+    if rate is None:
+        arrivals = np.zeros(count)
+    else:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+    return probs, arrivals
