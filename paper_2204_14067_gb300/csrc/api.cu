@@ -464,8 +464,9 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
         if (so.F_target > 0 && F <= so.F_target) { converged = true; break; }
         const double rel = std::fabs(F_prev - F) / (1.0 + std::fabs(F_prev));
         if (rel < so.tol) { converged = true; break; }
-        // BF16 gathers: the final iterations run in FP32 once progress stalls
-        if (h->opt.precision == 1 && !h->refine && rel < 1e-4) h->refine = true;
+        // BF16 gathers: the final iterations run in FP32 once progress reaches
+        // the BF16 noise level (relative change < 3e-3 or no decrease)
+        if (h->opt.precision == 1 && !h->refine && (rel < 3e-3 || F >= F_prev)) h->refine = true;
       }
       if (so.F_target > 0 && F_bm <= so.F_target) { converged = true; ended_on_bm = true; break; }
       F_prev = F;

@@ -27,7 +27,7 @@ using namespace bm;
 constexpr int kSlabs = 64;     // partial-sum slabs per problem
 constexpr int kScal = 16;      // device scalars per problem
 enum { S_F = 0, S_FENTRY, S_FIRST, S_BETA, S_GGPREV, S_STEP, S_FLAST, S_F_F, S_LS0, S_LS1, S_LS2, S_LS3 };
-enum { P_NW = 0, P_GG, P_GP, P_DOG, P_WDW, P_DD };  // partial-sum columns
+enum { P_NW = 0, P_GG, P_GP, P_DOG, P_GD, P_DD };  // partial-sum columns
 
 struct DenseP {
   float *W, *H, *gW, *gH, *DW, *DH, *gWp, *gHp;
@@ -75,7 +75,7 @@ __global__ void k_fix_batch(const FixP* __restrict__ fp, const int64_t* __restri
 }
 
 // Slab partials of the dense dot products of one problem (blockIdx.y).
-// phase 0: |W|^2+|H|^2, |g|^2, <g, g_prev>, <D, g>;  phase 1: <W,D>+<H,D>, |D|^2
+// phase 0: |W|^2+|H|^2, |g|^2, <g, g_prev>, <D, g>;  phase 1: <g, D>, |D|^2
 __global__ void __launch_bounds__(256) k_dots_batch(const DenseP* __restrict__ dp, int phase,
                                                      double* __restrict__ part) {
   __shared__ double sh[4][256];
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_dots_batch(const DenseP* __restrict__ d
       a2 += g.x * gp.x + g.y * gp.y + g.z * gp.z + g.w * gp.w;
       a3 += D.x * g.x + D.y * g.y + D.z * g.z + D.w * g.w;
     } else {
-      a0 += x.x * D.x + x.y * D.y + x.z * D.z + x.w * D.w;
+      a0 += g.x * D.x + g.y * D.y + g.z * D.z + g.w * D.w;
       a1 += D.x * D.x + D.y * D.y + D.z * D.z + D.w * D.w;
     }
   }
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256) k_dots_batch(const DenseP* __restrict__ d
     __syncthreads();
   }
   if (threadIdx.x < 4) {
-    const int col = phase == 0 ? threadIdx.x : (threadIdx.x < 2 ? P_WDW + threadIdx.x : -1);
+    const int col = phase == 0 ? threadIdx.x : (threadIdx.x < 2 ? P_GD + threadIdx.x : -1);
     if (col >= 0) part[((int64_t)blockIdx.y * kSlabs + blockIdx.x) * 8 + col] = sh[threadIdx.x][0];
   }
 }
@@ -246,10 +246,10 @@ __global__ void k_ctrl_step(const DenseP* __restrict__ dp, const double* __restr
   if (p >= count) return;
   double* s = scal + (int64_t)p * kScal;
   const double lam = dp[p].lam;
-  const double wdw = sum_part(part, p, P_WDW), dd = sum_part(part, p, P_DD);
+  const double gd = sum_part(part, p, P_GD), dd = sum_part(part, p, P_DD);
   double c[5];
   c[0] = s[S_F];
-  c[1] = s[S_LS0] + lam * wdw;
+  c[1] = gd;  // phi'(0) = <grad F, D>
   c[2] = 0.5 * s[S_LS1] + 0.5 * lam * dd;
   c[3] = s[S_LS2];
   c[4] = 0.5 * s[S_LS3];

@@ -391,28 +391,31 @@ __device__ __forceinline__ void rr_pair(int r, int k, int np, int& p, int& q) {
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __restrict__ S, int n, int max_sweeps,
                                                           double* __restrict__ evals, double* __restrict__ evecs,
                                                           int* __restrict__ status) {
-  extern __shared__ __align__(16) float jac_sm[];
+  extern __shared__ __align__(16) unsigned char jac_raw[];
+  T* jac_sm = reinterpret_cast<T*>(jac_raw);
   const int np = n + (n & 1);           // padded size (even)
-  float* A = jac_sm;                    // np x np
-  float* V = jac_sm + np * np;          // np x np, column j = vector j
-  __shared__ float cs_[kJacMax / 2], sn_[kJacMax / 2];
+  T* A = jac_sm;                        // np x np
+  T* V = jac_sm + np * np;              // np x np, column j = vector j
+  __shared__ T cs_[kJacMax / 2], sn_[kJacMax / 2];
   __shared__ int pp_[kJacMax / 2], qq_[kJacMax / 2];
   __shared__ int sh_rot;
-  __shared__ float sh_floor;
+  __shared__ T sh_floor;
+  const T eps = sizeof(T) == 8 ? (T)4e-15 : (T)1e-7;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int idx = tid; idx < np * np; idx += nt) {
     const int i = idx / np, j = idx - i * np;
-    A[idx] = (i < n && j < n) ? (float)(0.5 * (S[i * n + j] + S[j * n + i])) : 0.f;
-    V[idx] = i == j ? 1.f : 0.f;
+    A[idx] = (i < n && j < n) ? (T)(0.5 * (S[i * n + j] + S[j * n + i])) : (T)0;
+    V[idx] = i == j ? (T)1 : (T)0;
   }
   __syncthreads();
   if (tid == 0) {
-    float fro = 0.f;
+    T fro = 0;
     for (int idx = 0; idx < np * np; ++idx) fro += A[idx] * A[idx];
-    sh_floor = 1e-12f * sqrtf(fro);   // absolute floor for (near) null 2x2 blocks
+    sh_floor = eps * (T)1e-3 * sqrt(fro);   // absolute floor for (near) null 2x2 blocks
   }
   __syncthreads();
   const int half = np / 2;
@@ -425,13 +428,13 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __rest
         int p, q;
         rr_pair(r, tid, np, p, q);
         if (p > q) { const int t = p; p = q; q = t; }
-        const float apq = A[p * np + q], app = A[p * np + p], aqq = A[q * np + q];
-        float c = 1.f, s = 0.f;
-        const float thr = fmaxf(1.0e-7f * sqrtf(fabsf(app * aqq)), sh_floor);
-        if (fabsf(apq) > thr && apq != 0.f) {
-          const float th = (aqq - app) / (2.f * apq);
-          const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
-          c = rsqrtf(t * t + 1.f);
+        const T apq = A[p * np + q], app = A[p * np + p], aqq = A[q * np + q];
+        T c = 1, s = 0;
+        const T thr = fmax(eps * sqrt(fabs(app * aqq)), sh_floor);
+        if (fabs(apq) > thr && apq != (T)0) {
+          const T th = (aqq - app) / ((T)2 * apq);
+          const T t = (th >= (T)0 ? (T)1 : (T)-1) / (fabs(th) + sqrt(th * th + (T)1));
+          c = (T)1 / sqrt(t * t + (T)1);
           s = t * c;
           sh_rot = 1;
         }
@@ -444,10 +447,10 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __rest
       // rows p, q of A
       for (int idx = tid; idx < half * np; idx += nt) {
         const int k = idx / np, col = idx - k * np;
-        const float c = cs_[k], s = sn_[k];
-        if (s == 0.f) continue;
+        const T c = cs_[k], s = sn_[k];
+        if (s == (T)0) continue;
         const int p = pp_[k], q = qq_[k];
-        const float ap = A[p * np + col], aq = A[q * np + col];
+        const T ap = A[p * np + col], aq = A[q * np + col];
         A[p * np + col] = c * ap - s * aq;
         A[q * np + col] = s * ap + c * aq;
       }
@@ -455,13 +458,13 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __rest
       // columns p, q of A and V
       for (int idx = tid; idx < half * np; idx += nt) {
         const int k = idx / np, row = idx - k * np;
-        const float c = cs_[k], s = sn_[k];
-        if (s == 0.f) continue;
+        const T c = cs_[k], s = sn_[k];
+        if (s == (T)0) continue;
         const int p = pp_[k], q = qq_[k];
-        const float ap = A[row * np + p], aq = A[row * np + q];
+        const T ap = A[row * np + p], aq = A[row * np + q];
         A[row * np + p] = c * ap - s * aq;
         A[row * np + q] = s * ap + c * aq;
-        const float vp = V[row * np + p], vq = V[row * np + q];
+        const T vp = V[row * np + p], vq = V[row * np + q];
         V[row * np + p] = c * vp - s * vq;
         V[row * np + q] = s * vp + c * vq;
       }
@@ -471,17 +474,75 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __rest
   }
   // sort the first n diagonal entries descending (the padding index stays out)
   for (int i = tid; i < n; i += nt) {
-    const float di = A[i * np + i];
+    const T di = A[i * np + i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const float dj = A[j * np + j];
+      const T dj = A[j * np + j];
       rank += (dj > di) || (dj == di && j < i);
     }
     evals[rank] = (double)di;
-    if (!isfinite(di)) atomicOr(status, 2);
+    if (!isfinite((double)di)) atomicOr(status, 2);
     for (int q = 0; q < n; ++q) evecs[q * n + rank] = (double)V[q * np + i];
   }
   if (tid == 0 && sweep >= max_sweeps) atomicOr(status, 4);
+}
+
+// C = A^T B (FP64, n x n row-major), one thread per entry
+__global__ void k_small_mm_tn(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C, int n) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc += A[k * n + i] * B[k * n + j];
+    C[idx] = acc;
+  }
+}
+
+
+// ---------------------------------------------------------------- Cholesky QR step
+// T = R^{-1} with R^T R = S (upper Cholesky factor), S symmetric positive
+// definite (the Gram of an almost orthonormal block).  One block, FP32,
+// right-looking factorisation then one column of the inverse per thread.
+__global__ void __launch_bounds__(512) k_chol_inv(const double* __restrict__ S, int n, float* __restrict__ T, int ldt,
+                                                int* __restrict__ status) {
+  extern __shared__ __align__(16) float ch_sm[];
+  float* A = ch_sm;  // n x n, upper triangle holds R
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ float piv;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx - i * n;
+    A[idx] = (float)(0.5 * (S[i * n + j] + S[j * n + i]));
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const float a = A[j * n + j];
+      if (!(a > 0.f)) atomicOr(status, 8);
+      piv = a > 0.f ? sqrtf(a) : 1.f;
+      A[j * n + j] = piv;
+    }
+    __syncthreads();
+    for (int c = j + 1 + tid; c < n; c += nt) A[j * n + c] /= piv;
+    __syncthreads();
+    const int L = n - j - 1;
+    for (int idx = tid; idx < L * L; idx += nt) {
+      const int r = j + 1 + idx / L, c = j + 1 + idx % L;
+      if (c >= r) A[r * n + c] -= A[j * n + r] * A[j * n + c];
+    }
+    __syncthreads();
+  }
+  // X = R^{-1}: column c solves R x = e_c by back substitution (thread per column)
+  for (int c = tid; c < n; c += nt) {
+    for (int i = n - 1; i >= 0; --i) {
+      float acc = (i == c) ? 1.f : 0.f;
+      for (int k = i + 1; k <= c; ++k) acc -= A[i * n + k] * T[k * ldt + c];
+      T[i * ldt + c] = i > c ? 0.f : acc / A[i * n + i];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * ldt; idx += nt) {
+    const int i = idx / ldt, c = idx - i * ldt;
+    if (c >= n) T[idx] = 0.f;
+  }
 }
 
 // ---------------------------------------------------------------- small helpers
@@ -674,15 +735,40 @@ void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall&
 
 void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, bool dbl) {
   BM_REQUIRE(n >= 1 && n <= kEigMax, BM_ERR_INVALID, "eigensolver: size out of range");
+  const int npd = n + (n & 1);
+  if (dbl && (size_t)2 * npd * npd * sizeof(double) <= 200 * 1024 && !getenv("BM_EIG_QL64")) {
+    // FP64: FP32 QL for approximate vectors V, S' = V^T S V in FP64, FP64
+    // Jacobi sweeps on the almost diagonal S', vectors V * V'
+    w.scratch.alloc((size_t)3 * n * n);
+    double* V = w.scratch.get();
+    double* T1 = V + (size_t)n * n;
+    double* S2 = T1 + (size_t)n * n;
+    sym_eig_dev(h, w, S, n, evals, V, false);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n * n, 256), (int64_t)num_sms() * 4));
+    BM_LAUNCH(h, "eig64_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(S, V, T1, n, n, n, 0));
+    BM_LAUNCH(h, "eig64_rotate", k_small_mm_tn<<<g, 256, 0, h.stream>>>(V, T1, S2, n));
+    const size_t smem = (size_t)2 * npd * npd * sizeof(double);
+    w.status.alloc(1);
+    BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
+    BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BM_LAUNCH(h, "jacobi_eig_f64",
+              k_jacobi_eig<double><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, evals, T1, w.status.get()));
+    BM_LAUNCH(h, "eig64_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(V, T1, evecs, n, n, n, 0));
+    int st = 0;
+    BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    BM_CUDA(cudaStreamSynchronize(h.stream));
+    BM_REQUIRE(!(st & 2), BM_ERR_NUMERIC, "eigensolver: non-finite eigenvalue");
+    return;
+  }
   if (!dbl && n <= kJacMax && getenv("BM_EIG_JACOBI")) {
     // FP32: parallel Jacobi (one block, both matrices in shared memory)
     const int np = n + (n & 1);
     const size_t smem = (size_t)2 * np * np * sizeof(float);
     w.status.alloc(1);
     BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
-    BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     BM_LAUNCH(h, "jacobi_eig_f32",
-              k_jacobi_eig<<<1, kJacThreads, smem, h.stream>>>(S, n, 30, evals, evecs, w.status.get()));
+              k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S, n, 30, evals, evecs, w.status.get()));
     int st = 0;
     BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
     BM_CUDA(cudaStreamSynchronize(h.stream));
@@ -717,6 +803,19 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
   BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
   BM_CUDA(cudaStreamSynchronize(h.stream));
   BM_REQUIRE(st == 0, BM_ERR_NUMERIC, st & 2 ? "eigensolver: non-finite eigenvalue" : "eigensolver: QL did not converge");
+}
+
+void chol_inv_dev(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt) {
+  BM_REQUIRE(n >= 1 && n <= 200, BM_ERR_INVALID, "cholesky: size out of range");
+  const size_t smem = (size_t)n * n * sizeof(float);
+  w.status.alloc(1);
+  BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
+  BM_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BM_LAUNCH(h, "chol_inv", k_chol_inv<<<1, 512, smem, h.stream>>>(S, n, T, ldt, w.status.get()));
+  int st = 0;
+  BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+  BM_CUDA(cudaStreamSynchronize(h.stream));
+  BM_REQUIRE(st == 0, BM_ERR_NUMERIC, "cholesky: Gram matrix not positive definite");
 }
 
 void select_scale_dev(bm_ctx& h, const double* E, int n, int rows, const int* cols_h, const double* scale_h,

@@ -19,6 +19,7 @@ struct Tall {
 struct DenseWork {
   DevBuf<double> gram_part;   // slab partials of Grams
   DevBuf<int> status;         // eigensolver status flags
+  DevBuf<double> scratch;     // eigensolver work matrices
 };
 
 // C (a x b, FP64, row-major ldc = b) = A^T B, A: L x a, B: L x b.
@@ -39,6 +40,10 @@ void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall&
 // evals[n] (FP64), eigenvectors into evecs (n x n FP64 row-major, column j
 // = vector j).  Throws BM_ERR_NUMERIC if the QL iteration fails.
 void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, bool dbl);
+
+// T (n x n FP32, ld ldt) = R^{-1}, R^T R = S (S FP64 n x n, positive definite).
+// Throws BM_ERR_NUMERIC if a pivot is not positive.
+void chol_inv_dev(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt);
 
 // T (rows x cols FP32, ld) = E(0:rows, cols_idx) * diag(scale)  (E FP64 n x n)
 void select_scale_dev(bm_ctx& h, const double* E, int n, int rows, const int* cols_h, const double* scale_h,

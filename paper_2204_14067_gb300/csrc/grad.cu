@@ -289,9 +289,11 @@ void line_search_coeffs_dev(bm_ctx& h, double c[5]) {
   BM_CUDA(cudaStreamSynchronize(h.stream));
   const double lam = h.lambda;
   const int64_t mW = ix.m * h.ld, nH = ix.n * h.ld;
-  const double WDW = dot_dev(h, h.W.get(), h.DW.get(), mW) + dot_dev(h, h.H.get(), h.DH.get(), nH);
+  // phi'(0) = <grad F, D> from the gradient already in memory (h.gW, h.gH):
+  // equal to sum r b + lam (<W,DW> + <H,DH>) but free of its cancellation
+  const double GD = dot_dev(h, h.gW.get(), h.DW.get(), mW) + dot_dev(h, h.gH.get(), h.DH.get(), nH);
   const double DD = dot_dev(h, h.DW.get(), h.DW.get(), mW) + dot_dev(h, h.DH.get(), h.DH.get(), nH);
-  c[1] = sums[0] + lam * WDW;
+  c[1] = GD;
   c[2] = 0.5 * sums[1] + 0.5 * lam * DD;
   c[3] = sums[2];
   c[4] = 0.5 * sums[3];

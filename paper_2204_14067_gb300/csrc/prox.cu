@@ -139,19 +139,26 @@ int orth_dev(bm_ctx& h, const Tall& M, const Tall* F, const Tall* LM, const Tall
       if (LM) gemm_dev(h, *LF, ps.Ts.get(), ps.ldq2, mview(h, la, c1), 1.f, -1.f, "gemm_orth");
     }
     gram_dev(h, ps.dw, Mh, Mh, ps.G.get(), true, "gram_orth");
-    sym_eig_dev(h, ps.dw, ps.G.get(), c1, ps.ev.get(), ps.E.get(), false);  // FP32: drop test and scaling, pass 2 restores orthogonality
-    std::vector<double> lam = to_host(h, ps.ev.get(), c1);
-    std::vector<int> keep;
-    std::vector<double> s;
-    for (int j = 0; j < c1; ++j) {
-      if (!(lam[j] > tau)) break;
-      if (pass == 0 && max_cols >= 0 && j >= max_cols) break;
-      keep.push_back(j);
-      s.push_back(1.0 / std::sqrt(lam[j]));
+    int c2 = c1;
+    if (pass == 0) {
+      // Eq. "orth-W": eigen-decomposition of P^T P, drop eigenvalues <= tau, scale by Lambda^{-1/2}
+      sym_eig_dev(h, ps.dw, ps.G.get(), c1, ps.ev.get(), ps.E.get(), false);
+      std::vector<double> lam = to_host(h, ps.ev.get(), c1);
+      std::vector<int> keep;
+      std::vector<double> s;
+      for (int j = 0; j < c1; ++j) {
+        if (!(lam[j] > tau)) break;
+        if (max_cols >= 0 && j >= max_cols) break;
+        keep.push_back(j);
+        s.push_back(1.0 / std::sqrt(lam[j]));
+      }
+      c2 = (int)keep.size();
+      if (c2 == 0) return 0;
+      make_transform(h, ps.E.get(), c1, c1, keep, s);
+    } else {
+      // re-orthogonalisation of an almost orthonormal block: Cholesky QR, Q = P R^{-1}
+      chol_inv_dev(h, ps.dw, ps.G.get(), c1, ps.Ts.get(), ps.ldq2);
     }
-    const int c2 = (int)keep.size();
-    if (c2 == 0) return 0;
-    make_transform(h, ps.E.get(), c1, c1, keep, s);
     gemm_dev(h, Mh, ps.Ts.get(), ps.ldq2, mview(h, b, c2), 0.f, 1.f, "gemm_orth");
     if (LM) gemm_dev(h, mview(h, la, c1), ps.Ts.get(), ps.ldq2, mview(h, lb, c2), 0.f, 1.f, "gemm_orth");
     std::swap(a, b);

@@ -203,7 +203,8 @@ void run_batched(bm_server_ctx& s) {
           act[i].outer++;
           // BF16 gathers: the final iterations run in FP32 once progress stalls
           if (std::isfinite(act[i].F_prev) && act[i].h->opt.precision == 1 && !act[i].h->refine &&
-              std::fabs(act[i].F_prev - act[i].F) / (1.0 + std::fabs(act[i].F_prev)) < 1e-4)
+              (std::fabs(act[i].F_prev - act[i].F) / (1.0 + std::fabs(act[i].F_prev)) < 3e-3 ||
+               act[i].F >= act[i].F_prev))
             act[i].h->refine = true;
         }
       });
