@@ -127,6 +127,20 @@ def algorithmic_bytes(kernel, d, k, q):
     return None
 
 
+def measured_traffic(kernel, d, k):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary
+    (profiles/<kernel>_netflix_k<k>.txt, line 'dram_bytes_per_launch: N'),
+    or None when no capture of the current kernel exists."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_netflix_k{k}.txt")
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_launch:"):
+                return float(line.split(":", 1)[1])
+    except OSError:
+        return None
+    return None
+
+
 def algorithmic_flops(kernel, d, k, q):
     nnz = d["nnz"]
     if kernel in ("grad_csr", "grad_csc"):
@@ -221,12 +235,15 @@ def run_ours(args):
     if rank != 0:
         return None
     peaks, peak_kind = _load_peaks()
-    # dominant kernel
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else (None, (0, 0.0))
+    # dominant kernel: the largest total device time among kernels with a work model
+    modeled = {nm: v for nm, v in prof.items() if algorithmic_bytes(nm, d, 1, 1) is not None}
+    top_all = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    dom = max(modeled.items(), key=lambda kv: kv[1][1]) if modeled else (None, (0, 0.0))
     name, (launches, tot_ms) = dom
     q = k_now + 1
-    fl = algorithmic_flops(name, d, k_now if args.mode == "cycle" else k, q) if name else None
-    by = algorithmic_bytes(name, d, k_now if args.mode == "cycle" else k, q) if name else None
+    kk = k_now if args.mode == "cycle" else k
+    fl = algorithmic_flops(name, d, kk, q) if name else None
+    by = algorithmic_bytes(name, d, kk, q) if name else None
     avg_s = (tot_ms / launches) / 1e3 if launches else None
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock, TFLOP/s
@@ -234,21 +251,23 @@ def run_ours(args):
     if avg_s and fl is not None and by is not None:
         intensity = fl / by
         ridge = alu_peak * 1e12 / (float(peaks["hbm_gbs"]) * 1e9)
+        traffic = measured_traffic(name, d, kk)
         if intensity >= ridge:
             ach = fl / avg_s / 1e12
             roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": ach / alu_peak, "traffic": None,
+                    "frac": ach / alu_peak, "traffic": traffic,
                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                     "hbm_achieved_gbs": by / avg_s / 1e9, "hbm_peak_gbs": float(peaks["hbm_gbs"]),
                     "hbm_frac": by / avg_s / 1e9 / float(peaks["hbm_gbs"]), "hbm_peak_source": peak_kind}
         else:
             ach = by / avg_s / 1e9
             roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": float(peaks["hbm_gbs"]),
-                    "unit": "GB/s", "frac": ach / float(peaks["hbm_gbs"]), "traffic": None,
+                    "unit": "GB/s", "frac": ach / float(peaks["hbm_gbs"]), "traffic": traffic,
                     "peak_source": peak_kind}
         roof["bytes_per_launch"] = by
         roof["flops_per_launch"] = fl
         roof["avg_launch_ms"] = avg_s * 1e3
+        roof["top_kernel_overall"] = top_all
     cpu = cpu_baseline(p, args.mode) if not args.no_cpu else None
     line = {
         "metric": "BM gradient nnz/s" if args.mode == "grad" else "BM-Global cycle nnz/s",
