@@ -127,18 +127,21 @@ def algorithmic_bytes(kernel, d, k, q):
     return None
 
 
-def measured_traffic(kernel, d, k):
+def measured_traffic(kernel, d, k, panels=1):
     """DRAM bytes per launch of `kernel` from a committed ncu summary
-    (profiles/<kernel>_netflix_k<k>.txt, line 'dram_bytes_per_launch: N'),
-    or None when no capture of the current kernel exists."""
+    (profiles/<kernel>_netflix_k<k>.txt: 'dram_bytes_per_launch: N' taken with
+    'panels: P'), or None when no capture of the kernel as it runs exists."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_netflix_k{k}.txt")
+    got, cap_panels = None, None
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_launch:"):
-                return float(line.split(":", 1)[1])
+                got = float(line.split(":", 1)[1])
+            elif line.startswith("panels:"):
+                cap_panels = int(line.split(":", 1)[1])
     except OSError:
         return None
-    return None
+    return got if cap_panels == panels else None
 
 
 def algorithmic_flops(kernel, d, k, q):
@@ -171,6 +174,8 @@ def run_ours(args):
     k = min(K_BENCH, p.k_max)
     W0, H0 = random_factors(p.m, p.n, k, seed=11, scale=0.1)
     B.bm_set_factors(h, k, W0, H0)
+    # work-split autotuning of the sparse passes (panel order for L2 reuse)
+    tune = None if args.no_tune else B.bm_autotune(h)
 
     gWd = torch.empty((p.m, k), dtype=torch.float32, device="cuda")
     gHd = torch.empty((p.n, k), dtype=torch.float32, device="cuda")
@@ -251,7 +256,7 @@ def run_ours(args):
     if avg_s and fl is not None and by is not None:
         intensity = fl / by
         ridge = alu_peak * 1e12 / (float(peaks["hbm_gbs"]) * 1e9)
-        traffic = measured_traffic(name, d, kk)
+        traffic = measured_traffic(name, d, kk, tune[name][0] if tune and name in tune else 1)
         if intensity >= ridge:
             ach = fl / avg_s / 1e12
             roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
@@ -286,7 +291,8 @@ def run_ours(args):
                    "lambda": p.lam, "k": k, "k_end": k_now, "step": "3 BM iterations + 1 inexact PG step"
                    if args.mode == "cycle" else "one loss/gradient evaluation",
                    "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (1.6 GB of index per pass)",
-                   "generate_s": round(t_gen, 1)},
+                   "generate_s": round(t_gen, 1),
+                   "panels": ({nm: v[0] for nm, v in tune.items()} if tune else "natural split")},
         "e2e": {"value": e2e_val, "unit": "nnz/s",
                 "h2d_bytes_per_step": int(W0.nbytes + H0.nbytes),
                 "d2h_bytes_per_step": int(W0.nbytes + H0.nbytes)},
@@ -407,6 +413,7 @@ def main():
     ap.add_argument("--mode", default="cycle", choices=["cycle", "grad"])
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the natural work split (one panel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -65,6 +65,8 @@ typedef struct {
   int32_t k_init;        /* k_{-1}: sketch size of the initial PG step (Sec. "Initialization"); 8 */
   int32_t precision;     /* 0: FP32 factors; 1: BF16 factor copies for the gathers */
   uint64_t seed;         /* counter-based RNG key for the sketch and xi_t */
+  int32_t autotune;      /* 1: bm_solve runs bm_autotune once before its first cycle; 0 */
+  int32_t pad_;
 } bm_options;
 
 /* Result of one inexact PG step (Eq. "inexactpg", "truncate"). */
@@ -72,7 +74,7 @@ typedef struct {
   int32_t k_new;         /* rank of X_{t+1}: singular values surviving the threshold */
   int32_t warm_cols;     /* columns of the LmSVD warm start U^{t,0} */
   int32_t lmsvd_iters;   /* Rayleigh-Ritz steps taken */
-  int32_t n_L;           /* applications of L(U) = Z Z^T U */
+  int32_t n_L;           /* LmSVD block products with Z^T (each block of L(U) = Z Z^T U costs one) */
   int32_t cap_hit;       /* 1 if more than k_max values survived (rank capped) */
   int32_t pad_;
   double eps;            /* ||Z_t - Z~_t||_F (Sec. "Inexact PG step", monitoring formula) */
@@ -203,6 +205,39 @@ bm_status bm_prox_step(bm_handle h, double alpha, bm_prox_info* info);
  * max_outer or time_limit_s ended the solve.
  */
 bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info);
+
+/*
+ * Work-split tuning of the sparse passes (no counterpart in the paper; it
+ * changes the order of work, not the arithmetic of Eq. (MF) and (ZZ)).
+ * Pass kinds, in array order: 0 loss/gradient over rows (gathers H), 1
+ * gradient over columns (gathers W), 2 line-search sums over rows (gathers H
+ * and D_H), 3 the PG step's SpMM R Y over rows, 4 its SpMM R^T U over
+ * columns.  With P panels a pass visits its segments in P groups, each
+ * gathering from one P-th of the gathered block's rows, so the rows in use at
+ * any moment fit the 129 MB L2.  Results differ between panel counts only in
+ * the order of floating-point additions.
+ *
+ * bm_autotune times every kind with one panel and, where the gathered block
+ * exceeds a quarter of L2, with 2, 3, 4, 6, 8, 12, 16 panels (up to
+ * max_panels), and keeps the fastest; it needs factors (k >= 1), overwrites
+ * the gradient, search-direction and PG scratch buffers (not W, H or the PG
+ * warm-start state) and takes about 20 launches per kind.  info (nullable)
+ * receives the choice.  bm_set_panels fixes the counts (each in
+ * [1, BM_MAX_PANELS]); bm_get_panels reads them.  A batch (bm_batch_create)
+ * reads the counts when it is created.  Errors: BM_ERR_INVALID for a bad
+ * count or empty factors.
+ */
+#define BM_PASS_KINDS 5
+#define BM_MAX_PANELS 16
+typedef struct {
+  int32_t panels[BM_PASS_KINDS];   /* chosen panel count per pass kind */
+  int32_t timed;                   /* timed candidates */
+  double ms[BM_PASS_KINDS];        /* one launch with the chosen split (ms, fastest of 3) */
+  double ms_single[BM_PASS_KINDS]; /* one launch with one panel (ms, fastest of 3) */
+} bm_tune_info;
+bm_status bm_autotune(bm_handle h, int32_t max_panels, bm_tune_info* info);
+bm_status bm_set_panels(bm_handle h, const int32_t* panels);
+bm_status bm_get_panels(bm_handle h, int32_t* panels);
 
 /*
  * Batched BM phase over many solves.  A batch groups handles on one device

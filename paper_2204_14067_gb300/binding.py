@@ -34,7 +34,17 @@ class bm_options(ctypes.Structure):
                 ("lmsvd_p", ctypes.c_int32), ("lmsvd_imax", ctypes.c_int32), ("lmsvd_min_iter", ctypes.c_int32),
                 ("lmsvd_tol", ctypes.c_double), ("tau", ctypes.c_double), ("ritz_rel", ctypes.c_double),
                 ("psi0", ctypes.c_double), ("k_init", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("autotune", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+BM_PASS_KINDS = 5
+BM_MAX_PANELS = 16
+PASS_NAMES = ("grad_csr", "grad_csc", "linesearch_csr", "spmm_csr", "spmm_csc")
+
+
+class bm_tune_info(ctypes.Structure):
+    _fields_ = [("panels", ctypes.c_int32 * BM_PASS_KINDS), ("timed", ctypes.c_int32),
+                ("ms", ctypes.c_double * BM_PASS_KINDS), ("ms_single", ctypes.c_double * BM_PASS_KINDS)]
 
 
 class bm_prox_info(ctypes.Structure):
@@ -73,6 +83,9 @@ _SIGS = {
     "bm_prox_step": (_c.c_int, [_P, _c.c_double, _c.POINTER(bm_prox_info)]),
     "bm_solve": (_c.c_int, [_P, _c.POINTER(bm_solve_opts), _c.POINTER(bm_solve_info)]),
     "bm_profile_enable": (_c.c_int, [_P, _c.c_int32]),
+    "bm_autotune": (_c.c_int, [_P, _c.c_int32, _c.POINTER(bm_tune_info)]),
+    "bm_set_panels": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
+    "bm_get_panels": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_profile_read": (_c.c_int, [_P, _c.c_int32, _P, _P, _P, _P]),
 }
 
@@ -227,6 +240,26 @@ def bm_solve(h, max_outer=100, tol=1e-10, F_target=0.0, time_limit_s=0.0, raise_
         _check(st, h)
     return dict(outer=info.outer, k=info.k, converged=bool(info.converged), F=info.F, seconds=info.seconds,
                 status=st)
+
+
+def bm_autotune(h, max_panels=BM_MAX_PANELS):
+    """Time the sparse passes' work splits and keep the fastest; returns
+    {pass name: (panels, ms chosen, ms with one panel)}."""
+    info = bm_tune_info()
+    _check(lib().bm_autotune(h, int(max_panels), ctypes.byref(info)), h)
+    return {nm: (int(info.panels[i]), float(info.ms[i]), float(info.ms_single[i]))
+            for i, nm in enumerate(PASS_NAMES)}
+
+
+def bm_set_panels(h, panels):
+    arr = (ctypes.c_int32 * BM_PASS_KINDS)(*[int(x) for x in panels])
+    _check(lib().bm_set_panels(h, arr), h)
+
+
+def bm_get_panels(h):
+    arr = (ctypes.c_int32 * BM_PASS_KINDS)()
+    _check(lib().bm_get_panels(h, arr), h)
+    return [int(x) for x in arr]
 
 
 def bm_profile_enable(h, enable=True):

@@ -62,19 +62,7 @@ thread_local std::string g_last_error;
 
 template <class Fn>
 bm_status guarded(bm_ctx* h, Fn&& fn) {
-  try {
-    fn();
-    return BM_OK;
-  } catch (const Error& e) {
-    (h ? h->err : g_last_error) = e.msg;
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    (h ? h->err : g_last_error) = "host allocation failed";
-    return BM_ERR_OOM;
-  } catch (...) {
-    (h ? h->err : g_last_error) = "unexpected exception";
-    return BM_ERR_CUDA;
-  }
+  return guard_call(h ? h->err : g_last_error, std::forward<Fn>(fn));
 }
 
 // Copy `count` elements to a device buffer if `src` is host memory.
@@ -248,6 +236,7 @@ bm_status bm_default_options(bm_options* o) {
   o->psi0 = 0.1;
   o->k_init = 8;
   o->precision = 0;
+  o->autotune = 0;
   o->seed = 0;
   return BM_OK;
 }
@@ -298,14 +287,13 @@ bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, cons
     h->gWp.alloc(mW); h->gHp.alloc(nH);
     h->r_csr.alloc(std::max<int64_t>(1, nnz));
     h->r_csc.alloc(std::max<int64_t>(1, nnz));
-    h->sc.partial.alloc(std::max<int64_t>(1, std::max(ix.rs.nslots, ix.cs.nslots)) * h->ldmax);
     if (o.precision == 1) {
       const int64_t ldb = ((h->ldmax + 7) / 8) * 8;
       h->Wb.alloc(ix.m * ldb);
       h->Hb.alloc(ix.n * ldb);
       h->DHb.alloc(ix.n * ldb);
     }
-    h->sc.fseg.alloc(std::max(ix.rs.nseg, ix.cs.nseg) * 4 + 4);
+    ensure_pass_scratch(*h, h->ldmax);
     h->sc.red.alloc(4096);
     h->sc.scal.alloc(64);
     set_rank(*h, 0);
@@ -451,6 +439,7 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
     };
     bm_prox_info pi;
     if (h->k == 0) init_step_dev(*h, nullptr);
+    if (h->opt.autotune && !h->tuned && h->k > 0) autotune_dev(*h, BM_MAX_PANELS, nullptr);
     // F(X_t) is read from the first loss pass of each BM phase; the BM output
     // X~_t (F from its line search) is an iterate too and may end the solve.
     double F_prev = 0.0, F = 0.0;

@@ -36,6 +36,7 @@ struct DenseP {
   const double* fseg_csr;  // per-segment 1/2 sum r^2 of the CSR pass
   int64_t nseg_csr;
   const double* fseg_ls;   // per-segment line-search sums (4 each)
+  int64_t nseg_ls;
   uint16_t *Wb, *Hb, *DHb; // BF16 copies (nullable)
   int ld, ldb;
 };
@@ -123,7 +124,8 @@ __global__ void k_seg_sums_batch(const DenseP* __restrict__ dp, int phase, doubl
   __shared__ double sh[4][256];
   const DenseP& d = dp[blockIdx.x];
   double a[4] = {0, 0, 0, 0};
-  for (int64_t i = threadIdx.x; i < d.nseg_csr; i += blockDim.x) {
+  const int64_t nseg = phase == 0 ? d.nseg_csr : d.nseg_ls;
+  for (int64_t i = threadIdx.x; i < nseg; i += blockDim.x) {
     if (phase == 0) a[0] += d.fseg_csr[i];
     else for (int q = 0; q < 4; ++q) a[q] += d.fseg_ls[i * 4 + q];
   }
@@ -308,8 +310,8 @@ struct Group {  // problems that share a row width and gather type (one batched 
   bool bf;
   std::vector<int> members;
   DevBuf<PipeArgs> a_csr, a_csc, a_ls;
-  DevBuf<int64_t> pre_csr, pre_csc;
-  int64_t tot_csr = 0, tot_csc = 0;
+  DevBuf<int64_t> pre_csr, pre_csc, pre_ls;
+  int64_t tot_csr = 0, tot_csc = 0, tot_ls = 0;
 };
 
 }  // namespace
@@ -351,8 +353,9 @@ void build_tables(bm_batch_ctx& b) {
     d.nH = ix.n * h.ld;
     d.lam = h.lambda;
     d.fseg_csr = h.sc.fseg.get();
-    d.nseg_csr = ix.rs.nseg;
+    d.nseg_csr = pass_segs(ix, kPassGradCsr).nseg;
     d.fseg_ls = h.sc.fseg.get();
+    d.nseg_ls = pass_segs(ix, kPassLsCsr).nseg;
     d.ld = h.ld;
     d.ldb = ((h.ld + 7) / 8) * 8;
     d.Wb = h.Wb.get(); d.Hb = h.Hb.get(); d.DHb = h.DHb.get();
@@ -369,7 +372,7 @@ void build_tables(bm_batch_ctx& b) {
     }
     gr->members.push_back(p);
     for (int pass = 0; pass < 2; ++pass) {
-      const Segs& sg = pass == 0 ? ix.rs : ix.cs;
+      const Segs& sg = pass_segs(ix, pass == 0 ? kPassGradCsr : kPassGradCsc);
       if (!sg.nmulti) continue;
       FixP f{sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti, h.sc.partial.get(),
              pass == 0 ? h.W.get() : h.H.get(), h.ld, (float)h.lambda, pass == 0 ? h.gW.get() : h.gH.get()};
@@ -382,12 +385,12 @@ void build_tables(bm_batch_ctx& b) {
   for (auto& gp : b.groups) {
     Group& g = *gp;
     std::vector<PipeArgs> ac, ah, al;
-    std::vector<int64_t> pc{0}, ph{0};
+    std::vector<int64_t> pc{0}, ph{0}, pl{0};
     for (int p : g.members) {
       bm_ctx& h = *b.hs[p];
       const Index& ix = h.ix;
       for (int pass = 0; pass < 3; ++pass) {
-        const Segs& sg = pass == 1 ? ix.cs : ix.rs;
+        const Segs& sg = pass_segs(ix, pass == 0 ? kPassGradCsr : (pass == 1 ? kPassGradCsc : kPassLsCsr));
         PipeArgs a{};
         a.seg_row = sg.row.get();
         a.seg_beg = sg.beg.get();
@@ -416,19 +419,22 @@ void build_tables(bm_batch_ctx& b) {
           a.scal = h.r_csr.get(); a.o0 = h.W.get(); a.o1 = h.DW.get(); a.g0 = h.H.get(); a.g1 = h.DH.get();
           a.g0b = h.Hb.get(); a.g1b = h.DHb.get(); a.fseg = h.sc.fseg.get();
           al.push_back(a);
+          pl.push_back(pl.back() + sg.nseg);
         }
       }
     }
     const size_t np = g.members.size();
     g.a_csr.alloc(np); g.a_csc.alloc(np); g.a_ls.alloc(np);
-    g.pre_csr.alloc(np + 1); g.pre_csc.alloc(np + 1);
+    g.pre_csr.alloc(np + 1); g.pre_csc.alloc(np + 1); g.pre_ls.alloc(np + 1);
     BM_CUDA(cudaMemcpyAsync(g.a_csr.get(), ac.data(), np * sizeof(PipeArgs), cudaMemcpyHostToDevice, b.stream));
     BM_CUDA(cudaMemcpyAsync(g.a_csc.get(), ah.data(), np * sizeof(PipeArgs), cudaMemcpyHostToDevice, b.stream));
     BM_CUDA(cudaMemcpyAsync(g.a_ls.get(), al.data(), np * sizeof(PipeArgs), cudaMemcpyHostToDevice, b.stream));
     BM_CUDA(cudaMemcpyAsync(g.pre_csr.get(), pc.data(), (np + 1) * 8, cudaMemcpyHostToDevice, b.stream));
     BM_CUDA(cudaMemcpyAsync(g.pre_csc.get(), ph.data(), (np + 1) * 8, cudaMemcpyHostToDevice, b.stream));
+    BM_CUDA(cudaMemcpyAsync(g.pre_ls.get(), pl.data(), (np + 1) * 8, cudaMemcpyHostToDevice, b.stream));
     g.tot_csr = pc.back();
     g.tot_csc = ph.back();
+    g.tot_ls = pl.back();
     BM_CUDA(cudaStreamSynchronize(b.stream));
   }
   b.dense.alloc(b.count);
@@ -489,7 +495,7 @@ void enqueue_epoch(bm_batch_ctx& b) {
     BM_CHECK_LAUNCH();
   }
   for (auto& g : b.groups)
-    launch_direct_batch<2>(g->a_ls.get(), g->pre_csr.get(), (int)g->members.size(), g->tot_csr, g->nchunk, g->bf, st);
+    launch_direct_batch<2>(g->a_ls.get(), g->pre_ls.get(), (int)g->members.size(), g->tot_ls, g->nchunk, g->bf, st);
   BM_CHECK_LAUNCH();
   k_seg_sums_batch<<<b.count, 256, 0, st>>>(b.dense.get(), 1, b.scal.get());
   BM_CHECK_LAUNCH();

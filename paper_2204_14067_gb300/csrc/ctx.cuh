@@ -1,5 +1,10 @@
 // Handle state and the device routines shared between translation units.
 #pragma once
+#include <map>
+#include <memory>
+#include <new>
+#include <utility>
+
 #include "common.cuh"
 
 namespace bm {
@@ -22,6 +27,17 @@ struct Segs {
   int64_t nslots = 0;
 };
 
+// Sparse passes whose work split is chosen separately (bm_autotune).
+enum PassKind : int {
+  kPassGradCsr = 0,   // loss / gradient, rows (gathers H)
+  kPassGradCsc = 1,   // gradient, columns (gathers W)
+  kPassLsCsr = 2,     // line-search sums, rows (gathers H and D_H)
+  kPassSpmmCsr = 3,   // q-wide SpMM R Y, rows (gathers the n-side block)
+  kPassSpmmCsc = 4,   // q-wide SpMM R^T U, columns (gathers the m-side block)
+  kPassKinds = 5
+};
+inline bool pass_is_csr(int kind) { return kind == kPassGradCsr || kind == kPassLsCsr || kind == kPassSpmmCsr; }
+
 struct Index {
   int64_t m = 0, n = 0, nnz = 0;  // internal orientation, m <= n
   bool transposed = false;
@@ -31,10 +47,30 @@ struct Index {
   DevBuf<int64_t> csr2csc;        // CSC position of CSR entry e
   DevBuf<int32_t> csc2csr;        // CSR position of CSC entry q (residual permutation)
   Segs rs, cs;                    // CSR (rows) and CSC (columns) work splits
+  // Panel-ordered splits by panel count P >= 2: the gathered side is cut into
+  // P equal index ranges and the segments are ordered panel by panel (rows
+  // in order within a panel), so the warps running at any moment gather from
+  // one panel's rows, which can stay in L2.  A row's segments keep
+  // consecutive partial slots in entry order (same deterministic fix-up).
+  std::map<int, std::unique_ptr<Segs>> rsp, csp;
+  int panels[kPassKinds] = {1, 1, 1, 1, 1};   // panel count used by each pass kind
 };
+
+// The work split a pass kind uses (the natural one when its panel count is 1).
+inline const Segs& pass_segs(const Index& ix, int kind) {
+  const bool csr = pass_is_csr(kind);
+  const int P = ix.panels[kind];
+  if (P > 1) {
+    const auto& mp = csr ? ix.rsp : ix.csp;
+    auto it = mp.find(P);
+    if (it != mp.end()) return *it->second;
+  }
+  return csr ? ix.rs : ix.cs;
+}
 
 // Scratch reused across calls (sized once for the handle's k_max).
 struct Scratch {
+  int ld_part = 4;                // row width (floats) the partial buffer is sized for
   DevBuf<float> partial;          // segment partial sums
   DevBuf<double> fseg;            // per-segment loss partials
   DevBuf<double> red;             // block partials of dense reductions
@@ -89,9 +125,29 @@ struct bm_ctx {
   int ldb = 8;
   bm::DevBuf<uint16_t> Wb, Hb, DHb, Xb;
   bool bf_active() const { return opt.precision == 1 && !refine; }
+  bool tuned = false;            // panel counts chosen (bm_autotune / bm_set_panels)
 };
 
 namespace bm {
+
+// Run fn; a thrown Error, allocation failure or other exception becomes the
+// returned status and the message in err.
+template <class Fn>
+bm_status guard_call(std::string& err, Fn&& fn) {
+  try {
+    fn();
+    return BM_OK;
+  } catch (const Error& e) {
+    err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    err = "host allocation failed";
+    return BM_ERR_OOM;
+  } catch (...) {
+    err = "unexpected exception";
+    return BM_ERR_CUDA;
+  }
+}
 
 // Wrap a kernel launch with profiler events when profiling is on.
 #define BM_LAUNCH(h, name, ...)                              \
@@ -105,6 +161,15 @@ namespace bm {
 // index.cu
 void build_index(bm_ctx& h, int64_t m, int64_t n, int64_t nnz, const int32_t* rows_d,
                  const int32_t* cols_d, const float* vals_d);
+// Build (once) the P-panel split of one side and grow the partial / segment
+// scratch to fit it.
+void ensure_panel_segs(bm_ctx& h, bool csr, int P);
+// Largest slot and segment counts over all built splits.
+int64_t max_slots(const Index& ix);
+int64_t max_segs(const Index& ix);
+// Partial scratch for slot rows of width ld_part floats, segment scratch for
+// 4 doubles per segment (grown, never shrunk).
+void ensure_pass_scratch(bm_ctx& h, int ld_part);
 
 // grad.cu
 struct LossOut {
@@ -124,6 +189,9 @@ void ensure_bf16(bm_ctx& h);
 double residual_dev(bm_ctx& h);
 // Quartic coefficients c0..c4 of phi(s) along (h.DW, h.DH), using h.r_csr.
 void line_search_coeffs_dev(bm_ctx& h, double c[5]);
+// One launch of a sparse pass kind on the current state, for timing (loss /
+// gradient and line-search kinds; outputs land in the usual scratch).
+void tuning_pass_dev(bm_ctx& h, int kind);
 // Dense helpers over m x ld / n x ld arrays (deterministic FP64 reductions).
 double dot_dev(bm_ctx& h, const float* x, const float* y, int64_t count);
 void axpy_dev(bm_ctx& h, float* y, const float* x, float a, int64_t count);          // y += a x
@@ -137,6 +205,12 @@ void prox_destroy(bm_ctx& h);
 void prox_reset(bm_ctx& h);
 void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info);
 void init_step_dev(bm_ctx& h, bm_prox_info* info);
+// One q-wide SpMM of the PG step (CSR: R Y, CSC: R^T U) on scratch blocks of
+// width min(k_max + 1, k + 1), for timing.
+void tuning_spmm_dev(bm_ctx& h, bool csr);
+// Time every pass kind with panel counts 1..max_panels (only where the
+// gathered side exceeds a quarter of L2) and keep the fastest.
+void autotune_dev(bm_ctx& h, int max_panels, bm_tune_info* info);
 
 }  // namespace bm
 

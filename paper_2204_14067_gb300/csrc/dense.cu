@@ -17,103 +17,170 @@ __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpre
 __device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 
 // ---------------------------------------------------------------- Gram C = A^T B
-constexpr int kGramThreads = 256;
+// Each thread owns an 8 x 4 micro-tile of C (8 columns of A by 4 of B); a
+// block walks a slab of rows in tiles of kGramRows rows, double-buffered in
+// shared memory by cp.async.  Sums are unevaluated FP32 pairs (hi + lo), so
+// no FP64 arithmetic runs in the loop (FP64 is slow on this part): plain
+// Grams sum a tile in FP32 and add it to the pair by an error-free two-sum;
+// compensated Grams apply the error-free product and two-sum to every term
+// (Ogita-Rump-Oishi Dot2).  Slab partials leave as FP32 pairs.
 constexpr int kGramRows = 32;
+constexpr int kGramMaxThreads = 512;
 
-// Each block: a slab of rows, one group of 4x4 output micro-tiles per thread.
-// Within a tile of 32 rows sums are FP32 (compensated: Ogita-Rump-Oishi Dot2,
-// i.e. an error-free product and two-sum per term); tiles add into FP64.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+__device__ __forceinline__ float comp8(const float4& u, const float4& v, int i) {
+  return i < 4 ? comp(u, i) : comp(v, i - 4);
+}
+
 template <bool COMP>
-__global__ void __launch_bounds__(kGramThreads) k_gram(const float* __restrict__ A, int lda, int a,
-                                                       const float* __restrict__ B, int ldb, int b, int64_t L,
-                                                       int64_t slab, double* __restrict__ part) {
+__global__ void __launch_bounds__(kGramMaxThreads) k_gram(const float* __restrict__ A, int lda, int a,
+                                                          const float* __restrict__ B, int ldb, int b, int64_t L,
+                                                          int64_t slab, int sym, float2* __restrict__ part) {
   extern __shared__ float4 sm4[];
-  const int na = (a + 3) >> 2, nb = (b + 3) >> 2;
-  float4* As = sm4;
-  float4* Bs = sm4 + kGramRows * na;
-  const int mt = blockIdx.y * kGramThreads + threadIdx.x;
-  const bool active = mt < na * nb;
-  const int ti = active ? mt / nb : 0, tj = active ? mt % nb : 0;
-  double acc[16];
+  const int ng = (a + 7) >> 3, na = 2 * ng, a4 = (a + 3) >> 2, nb = (b + 3) >> 2;
+  const int stage = kGramRows * (na + nb);
+  const int mt = blockIdx.y * blockDim.x + threadIdx.x;
+  const int ti = mt < ng * nb ? mt / nb : 0, tj = mt < ng * nb ? mt % nb : 0;
+  // symmetric Grams (A = B): micro-tiles strictly below the diagonal are skipped
+  const bool active = mt < ng * nb && !(sym && 8 * ti > 4 * tj + 3);
+  float hi[32], lo[32];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int q = 0; q < 32; ++q) hi[q] = 0.f, lo[q] = 0.f;
   const int64_t r0 = (int64_t)blockIdx.x * slab;
   const int64_t r1 = min(L, r0 + slab);
-  for (int64_t rb = r0; rb < r1; rb += kGramRows) {
+  const int ntile = (int)((r1 - r0 + kGramRows - 1) / kGramRows);
+  auto load = [&](int t) {
+    float4* As = sm4 + (t & 1) * stage;
+    float4* Bs = As + kGramRows * na;
+    const int64_t rb = r0 + (int64_t)t * kGramRows;
     const int nr = (int)min((int64_t)kGramRows, r1 - rb);
-    for (int idx = threadIdx.x; idx < nr * na; idx += kGramThreads) {
+    for (int idx = threadIdx.x; idx < nr * na; idx += blockDim.x) {
       const int r = idx / na, c = idx - r * na;
-      As[r * na + c] = ldg4(A + (rb + r) * lda + 4 * c);
+      if (c < a4) cp_async16(reinterpret_cast<float*>(As + idx), A + (rb + r) * lda + 4 * c, true);
+      else As[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int idx = threadIdx.x; idx < nr * nb; idx += kGramThreads) {
+    for (int idx = threadIdx.x; idx < nr * nb; idx += blockDim.x) {
       const int r = idx / nb, c = idx - r * nb;
-      Bs[r * nb + c] = ldg4(B + (rb + r) * ldb + 4 * c);
+      cp_async16(reinterpret_cast<float*>(Bs + idx), B + (rb + r) * ldb + 4 * c, true);
     }
+  };
+  if (ntile > 0) load(0);
+  cp_async_commit();
+  for (int t = 0; t < ntile; ++t) {
+    if (t + 1 < ntile) load(t + 1);
+    cp_async_commit();
+    cp_async_wait<1>();
     __syncthreads();
+    const float4* As = sm4 + (t & 1) * stage;
+    const float4* Bs = As + kGramRows * na;
+    const int nr = (int)min((int64_t)kGramRows, r1 - (r0 + (int64_t)t * kGramRows));
     if (active) {
-      float s[16], lo[16];
+      if (COMP) {
+        for (int r = 0; r < nr; ++r) {
+          const float4 u = As[r * na + 2 * ti], v = As[r * na + 2 * ti + 1], bv = Bs[r * nb + tj];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) s[q] = 0.f, lo[q] = 0.f;
-      for (int r = 0; r < nr; ++r) {
-        const float4 av = As[r * na + ti];
-        const float4 bv = Bs[r * nb + tj];
+          for (int p = 0; p < 8; ++p) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float x = comp(av, p), y = comp(bv, q);
-            if (COMP) {
-              const float pr = x * y;
+            for (int q = 0; q < 4; ++q) {
+              const float x = comp8(u, v, p), y = comp(bv, q);
+              const float pr = __fmul_rn(x, y);
               const float pe = fmaf(x, y, -pr);
-              const float t = s[p * 4 + q] + pr;
-              const float z = t - s[p * 4 + q];
-              const float err = (s[p * 4 + q] - (t - z)) + (pr - z);
-              s[p * 4 + q] = t;
-              lo[p * 4 + q] += err + pe;
-            } else {
-              s[p * 4 + q] = fmaf(x, y, s[p * 4 + q]);
+              float s, e;
+              two_sum(hi[p * 4 + q], pr, s, e);
+              hi[p * 4 + q] = s;
+              lo[p * 4 + q] = __fadd_rn(lo[p * 4 + q], __fadd_rn(e, pe));
             }
           }
         }
-      }
+      } else {
+        float s[32];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] += (double)s[q] + (double)lo[q];
+        for (int q = 0; q < 32; ++q) s[q] = 0.f;
+        for (int r = 0; r < nr; ++r) {
+          const float4 u = As[r * na + 2 * ti], v = As[r * na + 2 * ti + 1], bv = Bs[r * nb + tj];
+#pragma unroll
+          for (int p = 0; p < 8; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[p * 4 + q] = fmaf(comp8(u, v, p), comp(bv, q), s[p * 4 + q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          float t2, e;
+          two_sum(hi[q], s[q], t2, e);
+          hi[q] = t2;
+          lo[q] = __fadd_rn(lo[q], e);
+        }
+      }
     }
     __syncthreads();
   }
   if (active) {
-    double* out = part + (int64_t)blockIdx.x * a * b;
+    float2* out = part + (int64_t)blockIdx.x * a * b;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 8; ++p)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int i = 4 * ti + p, j = 4 * tj + q;
-        if (i < a && j < b) out[i * b + j] = acc[p * 4 + q];
+        const int i = 8 * ti + p, j = 4 * tj + q;
+        if (i < a && j < b) out[i * b + j] = make_float2(hi[p * 4 + q], lo[p * 4 + q]);
       }
   }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int slabs, int ab, double* __restrict__ C) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ab; e += gridDim.x * blockDim.x) {
+// C[e] = sum over slabs of the FP32-pair partials, in slab order: warp w of a
+// block adds slabs w, w + 8, ... of 32 consecutive entries, then the eight
+// warp sums are added in warp order.  Symmetric Grams read entry (j, i) for i > j.
+__global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ part, int slabs, int a, int b,
+                                                     int sym, double* __restrict__ C) {
+  __shared__ float2 red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ab = a * b;
+  const int e = blockIdx.x * 32 + lane;
+  int src = e;
+  if (e < ab && sym) {
+    const int i = e / b, j = e - (e / b) * b;
+    if (i > j) src = j * b + i;
+  }
+  float hi = 0.f, lo = 0.f;
+  if (e < ab) {
+    for (int g = warp; g < slabs; g += 8) {
+      const float2 p = part[(int64_t)g * ab + src];
+      float s, err;
+      two_sum(hi, p.x, s, err);
+      hi = s;
+      lo = __fadd_rn(lo, __fadd_rn(err, p.y));
+    }
+  }
+  red[warp][lane] = make_float2(hi, lo);
+  __syncthreads();
+  if (warp == 0 && e < ab) {
     double s = 0.0;
-    for (int g = 0; g < slabs; ++g) s += part[(int64_t)g * ab + e];
+    for (int w = 0; w < 8; ++w) s += (double)red[w][lane].x + (double)red[w][lane].y;
     C[e] = s;
   }
 }
 
 // ---------------------------------------------------------------- Y = beta Y + gamma A C
+// A persistent block walks row tiles of R = 8 * groups rows.  C (a x b) stays
+// in shared memory for the whole launch; each A tile is staged transposed
+// (column t of the tile is R contiguous floats), so a thread owning 8 rows x 4
+// columns of Y issues two 16-byte loads of A and one of C per 32 FMAs.
 constexpr int kGemmThreads = 256;
 
-__global__ void __launch_bounds__(kGemmThreads) k_gemm(const float* __restrict__ A, int lda, int a,
-                                                       const float* __restrict__ C, int ldc, int b,
-                                                       float* __restrict__ Y, int ldy, int64_t L, float beta,
-                                                       float gamma) {
+__global__ void __launch_bounds__(kGemmThreads, 3) k_gemm(const float* __restrict__ A, int lda, int a,
+                                                          const float* __restrict__ C, int ldc, int b,
+                                                          float* __restrict__ Y, int ldy, int64_t L, float beta,
+                                                          float gamma, int groups) {
   extern __shared__ float4 gsm[];
   const int nb4 = (b + 3) >> 2, a4 = (a + 3) >> 2;
-  const int rpb = kGemmThreads / nb4;
-  float4* Cs = gsm;                  // a x nb4
-  float* As = reinterpret_cast<float*>(gsm + (size_t)a * nb4);  // rpb x (4*a4)
-  for (int idx = threadIdx.x; idx < a * nb4; idx += kGemmThreads) {
+  const int R = 8 * groups;
+  float4* Cs = gsm;                                              // a x nb4
+  float* At = reinterpret_cast<float*>(gsm + (size_t)a * nb4);   // (4 a4) x R, transposed tile
+  for (int idx = threadIdx.x; idx < a * nb4; idx += blockDim.x) {
     const int t = idx / nb4, c = idx - t * nb4;
     float4 v;
     v.x = 4 * c + 0 < b ? C[t * ldc + 4 * c + 0] : 0.f;
@@ -122,35 +189,53 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const float* __restrict__
     v.w = 4 * c + 3 < b ? C[t * ldc + 4 * c + 3] : 0.f;
     Cs[idx] = v;
   }
-  const int rr = threadIdx.x / nb4, cj = threadIdx.x - rr * nb4;
-  for (int64_t r0 = (int64_t)blockIdx.x * rpb; r0 < L; r0 += (int64_t)gridDim.x * rpb) {
+  const int g = threadIdx.x / nb4, cj = threadIdx.x - g * nb4;
+  const bool owner = g < groups;
+  for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < L; r0 += (int64_t)gridDim.x * R) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < rpb * a4; idx += kGemmThreads) {
-      const int r = idx / a4, c = idx - r * a4;
+    // rows vary fastest so that the transposed stores hit consecutive banks
+    for (int idx = threadIdx.x; idx < R * a4; idx += blockDim.x) {
+      const int c = idx / R, r = idx - c * R;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (r0 + r < L) v = ldg4(A + (r0 + r) * lda + 4 * c);
-      reinterpret_cast<float4*>(As)[idx] = v;
+      At[(4 * c + 0) * R + r] = v.x;
+      At[(4 * c + 1) * R + r] = v.y;
+      At[(4 * c + 2) * R + r] = v.z;
+      At[(4 * c + 3) * R + r] = v.w;
     }
     __syncthreads();
-    if (rr < rpb && r0 + rr < L) {
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float* ar = As + rr * 4 * a4;
+    if (owner) {
+      float4 acc[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float* ap = At + 8 * g;
       for (int t = 0; t < a; ++t) {
-        const float x = ar[t];
+        const float4 x0 = *reinterpret_cast<const float4*>(ap + t * R);
+        const float4 x1 = *reinterpret_cast<const float4*>(ap + t * R + 4);
         const float4 cv = Cs[t * nb4 + cj];
-        acc.x = fmaf(x, cv.x, acc.x);
-        acc.y = fmaf(x, cv.y, acc.y);
-        acc.z = fmaf(x, cv.z, acc.z);
-        acc.w = fmaf(x, cv.w, acc.w);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const float x = comp8(x0, x1, p);
+          acc[p].x = fmaf(x, cv.x, acc[p].x);
+          acc[p].y = fmaf(x, cv.y, acc[p].y);
+          acc[p].z = fmaf(x, cv.z, acc[p].z);
+          acc[p].w = fmaf(x, cv.w, acc[p].w);
+        }
       }
-      float4* yp = reinterpret_cast<float4*>(Y + (r0 + rr) * ldy + 4 * cj);
-      float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (beta != 0.f) y = *yp;
-      y.x = fmaf(gamma, acc.x, beta * y.x);
-      y.y = fmaf(gamma, acc.y, beta * y.y);
-      y.z = fmaf(gamma, acc.z, beta * y.z);
-      y.w = fmaf(gamma, acc.w, beta * y.w);
-      *yp = y;
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const int64_t row = r0 + 8 * g + p;
+        if (row < L) {
+          float4* yp = reinterpret_cast<float4*>(Y + row * ldy + 4 * cj);
+          float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (beta != 0.f) y = *yp;
+          y.x = fmaf(gamma, acc[p].x, beta * y.x);
+          y.y = fmaf(gamma, acc[p].y, beta * y.y);
+          y.z = fmaf(gamma, acc[p].z, beta * y.z);
+          y.w = fmaf(gamma, acc[p].w, beta * y.w);
+          *yp = y;
+        }
+      }
     }
   }
 }
@@ -174,6 +259,20 @@ __global__ void k_spmm_fixup(const int32_t* __restrict__ mrow, const int32_t* __
 // ---------------------------------------------------------------- symmetric eigensolver
 constexpr int kEigMax = 256;
 constexpr int kEigThreads = 512;
+
+// 1/sqrt(x) for x > 0: the hardware estimate refined by one Newton-Raphson
+// step y <- y (3 - x y^2) / 2 (FP32); FP64 uses rsqrt directly.
+template <typename T>
+__device__ __forceinline__ T rsqrt_refined(T x);
+template <>
+__device__ __forceinline__ float rsqrt_refined<float>(float x) {
+  const float y = rsqrtf(x);
+  return y * fmaf(-0.5f * x, y * y, 1.5f);
+}
+template <>
+__device__ __forceinline__ double rsqrt_refined<double>(double x) {
+  return rsqrt(x);
+}
 
 template <typename T>
 __device__ T block_sum(T v, T* red) {
@@ -279,65 +378,91 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
     }
     __syncthreads();
   }
-  // ---- implicit QL with shifts
+  // ---- implicit QL with shifts on T / ||T|| (entries of magnitude <= 1, so
+  // the rotation norms sqrt(f^2 + g^2) neither overflow nor need hypot).
+  // Warp 0 finds the end m of the unreduced block with a ballot; lane 0 then
+  // computes the sweep's rotations (d[i], e[i] prefetched one step ahead);
+  // all threads apply them to the rows of Z^T.
   if (tid == 0) {
     sh_state = 0;
     T an = 0;
     for (int i = 0; i < n; ++i) an = fmax(an, fabs(d[i]) + fabs(e[i]) + (i ? fabs(e[i - 1]) : (T)0));
     sh_anorm = an;
+    const T inv = an > 0 ? (T)1 / an : (T)1;
+    for (int i = 0; i < n; ++i) d[i] *= inv, e[i] *= inv;
   }
   __syncthreads();
+  const T scale = sh_anorm > 0 ? sh_anorm : (T)1;
+  const int lane = tid & 31;
   for (int l = 0; l < n; ++l) {
     int iter = 0;
     while (true) {
-      if (tid == 0) {
-        int m = l;
-        for (; m < n - 1; ++m) {
-          const T dd = fabs(d[m]) + fabs(d[m + 1]);
-          // relative test, with an absolute floor eps*||T|| so that (near) zero
-          // eigenvalues deflate as well
-          if (fabs(e[m]) <= eps * dd || fabs(e[m]) <= eps * sh_anorm) break;
+      if (tid < 32) {
+        int m = n - 1;
+        for (int base = l; base < n - 1; base += 32) {
+          const int mm = base + lane;
+          bool small = false;
+          if (mm < n - 1) {
+            const T em = fabs(e[mm]);
+            small = em <= eps * (fabs(d[mm]) + fabs(d[mm + 1])) || em <= eps;
+          }
+          const unsigned bal = __ballot_sync(kFull, small);
+          if (bal) {
+            m = base + __ffs(bal) - 1;
+            break;
+          }
         }
-        sh_m = m;
-        sh_cnt = 0;
-        if (m != l) {
-          if (++iter > 60) {
-            sh_state = 1;
-            sh_m = l;
-          } else {
-            T g = (d[l + 1] - d[l]) / ((T)2 * e[l]);
-            T r = hypot(g, (T)1);
-            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
-            T s = 1, c = 1, p = 0;
-            bool early = false;
-            int cnt = 0;
-            for (int i = m - 1; i >= l; --i) {
-              const T f = s * e[i], b = c * e[i];
-              r = hypot(f, g);
-              e[i + 1] = r;
-              if (r == (T)0) {
-                d[i + 1] -= p;
-                e[m] = 0;
-                early = true;
-                break;
+        if (lane == 0) {
+          sh_m = m;
+          sh_cnt = 0;
+          if (m != l) {
+            if (++iter > 60) {
+              sh_state = 1;
+              sh_m = l;
+            } else {
+              T g = (d[l + 1] - d[l]) / ((T)2 * e[l]);
+              T r = sqrt(g * g + (T)1);
+              g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+              T s = 1, c = 1, p = 0;
+              bool early = false;
+              int cnt = 0;
+              T ei = e[m - 1], di = d[m - 1], dn = d[m];
+              for (int i = m - 1; i >= l; --i) {
+                const T ei_next = i > l ? e[i - 1] : (T)0, di_next = i > l ? d[i - 1] : (T)0;
+                const T f = s * ei, b = c * ei;
+                const T t2 = fma(f, f, g * g);
+                if (!(t2 > (T)(sizeof(T) == 8 ? 1e-200 : 1e-30))) {
+                  // the rotation is the identity: split at i + 1
+                  e[i + 1] = (T)0;
+                  d[i + 1] = dn - p;
+                  e[m] = 0;
+                  early = true;
+                  break;
+                }
+                const T y = rsqrt_refined(t2);
+                r = t2 * y;
+                s = f * y;
+                c = g * y;
+                e[i + 1] = r;
+                g = dn - p;
+                r = (di - g) * s + (T)2 * c * b;
+                p = s * r;
+                d[i + 1] = g + p;
+                g = c * r - b;
+                cs[cnt] = c;
+                sn[cnt] = s;
+                ++cnt;
+                ei = ei_next;
+                dn = di;
+                di = di_next;
               }
-              s = f / r;
-              c = g / r;
-              g = d[i + 1] - p;
-              r = (d[i] - g) * s + (T)2 * c * b;
-              p = s * r;
-              d[i + 1] = g + p;
-              g = c * r - b;
-              cs[cnt] = c;
-              sn[cnt] = s;
-              ++cnt;
+              if (!early) {
+                d[l] -= p;
+                e[l] = g;
+                e[m] = 0;
+              }
+              sh_cnt = cnt;
             }
-            if (!early) {
-              d[l] -= p;
-              e[l] = g;
-              e[m] = 0;
-            }
-            sh_cnt = cnt;
           }
         }
       }
@@ -345,16 +470,20 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
       const int m = sh_m, cnt = sh_cnt;
       if (m == l) break;
       for (int q = tid; q < n; q += nt) {
+        T zf = Z[m * n + q];
         for (int t = 0; t < cnt; ++t) {
           const int i = m - 1 - t;
-          const T zi = Z[i * n + q], zf = Z[(i + 1) * n + q];
+          const T zi = Z[i * n + q];
           Z[(i + 1) * n + q] = sn[t] * zi + cs[t] * zf;
-          Z[i * n + q] = cs[t] * zi - sn[t] * zf;
+          zf = cs[t] * zi - sn[t] * zf;
         }
+        Z[(m - cnt) * n + q] = zf;
       }
       __syncthreads();
     }
   }
+  for (int i = tid; i < n; i += nt) d[i] *= scale;
+  __syncthreads();
   // ---- sort descending and write out
   for (int i = tid; i < n; i += nt) {
     const T di = d[i];
@@ -653,22 +782,30 @@ void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, 
     BM_CUDA(cudaMemsetAsync(C, 0, (size_t)a * b * sizeof(double), h.stream));
     return;
   }
-  const int na = (a + 3) / 4, nb = (b + 3) / 4;
-  int64_t gx = std::min<int64_t>(ceil_div(L, 64), (int64_t)2 * num_sms());
-  int64_t slab = ceil_div(ceil_div(L, gx), kGramRows) * kGramRows;
+  const int sym = (A.p == B.p && A.ld == B.ld && a == b) ? 1 : 0;
+  const int ng = (a + 7) / 8, nb = (b + 3) / 4;
+  const int tiles = ng * nb;
+  const int gy = (tiles + kGramMaxThreads - 1) / kGramMaxThreads;
+  const int threads = (int)(ceil_div(ceil_div(tiles, gy), 32) * 32);
+  // about three blocks per SM in total
+  int64_t gx = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 64), (int64_t)3 * num_sms() / gy));
+  const int64_t slab = ceil_div(ceil_div(L, gx), kGramRows) * kGramRows;
   gx = ceil_div(L, slab);
-  const int gy = (int)ceil_div((int64_t)na * nb, kGramThreads);
+  static_assert(sizeof(double) == sizeof(float2), "FP32-pair partials share the FP64 scratch");
   w.gram_part.alloc((size_t)gx * a * b);
-  const size_t smem = (size_t)kGramRows * (na + nb) * sizeof(float4);
+  const size_t smem = (size_t)2 * kGramRows * (2 * ng + nb) * sizeof(float4);
+  BM_REQUIRE(smem <= 200 * 1024, BM_ERR_INVALID, "gram: block too wide");
+  float2* part = reinterpret_cast<float2*>(w.gram_part.get());
   dim3 grid((unsigned)gx, (unsigned)gy);
   if (compensated) {
-    BM_LAUNCH(h, tag, k_gram<true><<<grid, kGramThreads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab,
-                                                                        w.gram_part.get()));
+    BM_CUDA(cudaFuncSetAttribute(k_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    BM_LAUNCH(h, tag, k_gram<true><<<grid, threads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab, sym, part));
   } else {
-    BM_LAUNCH(h, tag, k_gram<false><<<grid, kGramThreads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab,
-                                                                         w.gram_part.get()));
+    BM_CUDA(cudaFuncSetAttribute(k_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    BM_LAUNCH(h, tag, k_gram<false><<<grid, threads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab, sym, part));
   }
-  BM_LAUNCH(h, "gram_reduce", k_gram_reduce<<<grid1(a * b), 256, 0, h.stream>>>(w.gram_part.get(), (int)gx, a * b, C));
+  BM_LAUNCH(h, "gram_reduce", k_gram_reduce<<<(unsigned)ceil_div((int64_t)a * b, 32), 256, 0, h.stream>>>(
+                                  part, (int)gx, a, b, sym, C));
 }
 
 void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, float beta, float gamma,
@@ -681,18 +818,19 @@ void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, 
   }
   const int nb4 = (b + 3) / 4, a4 = (a + 3) / 4;
   BM_REQUIRE(nb4 <= kGemmThreads, BM_ERR_INVALID, "gemm: too many columns");
-  const int rpb = kGemmThreads / nb4;
-  const size_t smem = (size_t)a * nb4 * sizeof(float4) + (size_t)rpb * a4 * sizeof(float4);
-  BM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  const int groups = std::max(1, std::min(32, kGemmThreads / nb4));
+  const int R = 8 * groups;
+  const size_t smem = (size_t)a * nb4 * sizeof(float4) + (size_t)4 * a4 * R * sizeof(float);
   BM_REQUIRE(smem <= 200 * 1024, BM_ERR_INVALID, "gemm: block too large");
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A.rows, rpb), (int64_t)num_sms() * 8));
+  BM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A.rows, R), (int64_t)num_sms() * 3));
   BM_LAUNCH(h, tag, k_gemm<<<grid, kGemmThreads, smem, h.stream>>>(A.p, A.ld, a, C, ldc, b, Y.p, Y.ld, A.rows,
-                                                                   beta, gamma));
+                                                                   beta, gamma, groups));
 }
 
 void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall& Out, float gamma) {
   const Index& ix = h.ix;
-  const Segs& sg = csr ? ix.rs : ix.cs;
+  const Segs& sg = pass_segs(ix, csr ? kPassSpmmCsr : kPassSpmmCsc);
   if (X.cols == 0) return;
   PipeArgs a{};
   a.seg_row = sg.row.get();
@@ -733,33 +871,43 @@ void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall&
   }
 }
 
-void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, bool dbl) {
+void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, EigMode mode) {
   BM_REQUIRE(n >= 1 && n <= kEigMax, BM_ERR_INVALID, "eigensolver: size out of range");
   const int npd = n + (n & 1);
-  if (dbl && (size_t)2 * npd * npd * sizeof(double) <= 200 * 1024 && !getenv("BM_EIG_QL64")) {
-    // FP64: FP32 QL for approximate vectors V, S' = V^T S V in FP64, FP64
-    // Jacobi sweeps on the almost diagonal S', vectors V * V'
+  const bool jac64 = mode == kEigDouble && (size_t)2 * npd * npd * sizeof(double) <= 200 * 1024;
+  const bool jac32 = mode == kEigRelative && npd <= kJacMax;
+  if (jac64 || jac32) {
+    // FP32 QL for approximate vectors V, S' = V^T S V in FP64, Jacobi sweeps
+    // on the almost diagonal S' (FP64 or FP32), vectors V * V'
     w.scratch.alloc((size_t)3 * n * n);
     double* V = w.scratch.get();
     double* T1 = V + (size_t)n * n;
     double* S2 = T1 + (size_t)n * n;
-    sym_eig_dev(h, w, S, n, evals, V, false);
+    sym_eig_dev(h, w, S, n, evals, V, kEigFast);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n * n, 256), (int64_t)num_sms() * 4));
-    BM_LAUNCH(h, "eig64_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(S, V, T1, n, n, n, 0));
-    BM_LAUNCH(h, "eig64_rotate", k_small_mm_tn<<<g, 256, 0, h.stream>>>(V, T1, S2, n));
-    const size_t smem = (size_t)2 * npd * npd * sizeof(double);
+    BM_LAUNCH(h, "eig_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(S, V, T1, n, n, n, 0));
+    BM_LAUNCH(h, "eig_rotate", k_small_mm_tn<<<g, 256, 0, h.stream>>>(V, T1, S2, n));
     w.status.alloc(1);
     BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
-    BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    BM_LAUNCH(h, "jacobi_eig_f64",
-              k_jacobi_eig<double><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, evals, T1, w.status.get()));
-    BM_LAUNCH(h, "eig64_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(V, T1, evecs, n, n, n, 0));
+    if (jac64) {
+      const size_t smem = (size_t)2 * npd * npd * sizeof(double);
+      BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      BM_LAUNCH(h, "jacobi_eig_f64",
+                k_jacobi_eig<double><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, evals, T1, w.status.get()));
+    } else {
+      const size_t smem = (size_t)2 * npd * npd * sizeof(float);
+      BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      BM_LAUNCH(h, "jacobi_eig_rel",
+                k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, evals, T1, w.status.get()));
+    }
+    BM_LAUNCH(h, "eig_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(V, T1, evecs, n, n, n, 0));
     int st = 0;
     BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
     BM_CUDA(cudaStreamSynchronize(h.stream));
     BM_REQUIRE(!(st & 2), BM_ERR_NUMERIC, "eigensolver: non-finite eigenvalue");
     return;
   }
+  const bool dbl = mode != kEigFast;
   if (!dbl && n <= kJacMax && getenv("BM_EIG_JACOBI")) {
     // FP32: parallel Jacobi (one block, both matrices in shared memory)
     const int np = n + (n & 1);

@@ -35,11 +35,22 @@ void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, 
 // segment split (CSR: i = row, idx = col; CSC: i = col, idx = row).
 void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall& Out, float gamma);
 
+// Accuracy modes of the symmetric eigensolver.
+//  kEigFast: FP32 Householder + QL; eigenvalue errors ~ eps32 * ||S||.
+//  kEigRelative: kEigFast vectors V, S' = V^T S V in FP64, then FP32 Jacobi
+//    sweeps on S' with the relative rotation test |s_pq| > eps sqrt(s_pp s_qq);
+//    for positive semidefinite S this resolves each eigenvalue to a relative
+//    accuracy set by the conditioning of the diagonally scaled S' (Demmel and
+//    Veselic, "Jacobi's method is more accurate than QR", 1992), so small
+//    eigenvalues far below eps32 * ||S|| stay accurate.
+//  kEigDouble: as kEigRelative with FP64 Jacobi sweeps.
+enum EigMode { kEigFast = 0, kEigRelative = 1, kEigDouble = 2 };
+
 // Symmetric eigendecomposition of S (n x n FP64, row-major, symmetrised on
-// load) in precision `dbl` (FP64) or FP32: eigenvalues descending into
-// evals[n] (FP64), eigenvectors into evecs (n x n FP64 row-major, column j
-// = vector j).  Throws BM_ERR_NUMERIC if the QL iteration fails.
-void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, bool dbl);
+// load): eigenvalues descending into evals[n] (FP64), eigenvectors into evecs
+// (n x n FP64 row-major, column j = vector j).  Throws BM_ERR_NUMERIC if the
+// iteration fails.
+void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals, double* evecs, EigMode mode);
 
 // T (n x n FP32, ld ldt) = R^{-1}, R^T R = S (S FP64 n x n, positive definite).
 // Throws BM_ERR_NUMERIC if a pivot is not positive.

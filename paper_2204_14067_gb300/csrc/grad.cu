@@ -123,7 +123,7 @@ __global__ void k_xpby(float* __restrict__ y, const float* __restrict__ x, float
 
 void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
   const Index& ix = h.ix;
-  const Segs& sg = csr ? ix.rs : ix.cs;
+  const Segs& sg = pass_segs(ix, csr ? kPassGradCsr : kPassGradCsc);
   PipeArgs a{};
   a.seg_row = sg.row.get();
   a.seg_beg = sg.beg.get();
@@ -197,7 +197,7 @@ LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r) {
   LossOut o{0, 0, 0};
   double* fseg = h.sc.fseg.get();
   run_pass(h, true, store_r, fseg);
-  k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, ix.rs.nseg, 1, 0, h.sc.scal.get() + 1);
+  k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, pass_segs(ix, kPassGradCsr).nseg, 1, 0, h.sc.scal.get() + 1);
   BM_CHECK_LAUNCH();
   if (want_grad) run_pass(h, false, false, nullptr);
   BM_CUDA(cudaMemcpyAsync(&o.f, h.sc.scal.get() + 1, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
@@ -241,7 +241,7 @@ double residual_dev(bm_ctx& h) {
   const Index& ix = h.ix;
   double* fseg = h.sc.fseg.get();
   run_pass(h, true, true, fseg);
-  k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, ix.rs.nseg, 1, 0, h.sc.scal.get() + 1);
+  k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, pass_segs(ix, kPassGradCsr).nseg, 1, 0, h.sc.scal.get() + 1);
   BM_CHECK_LAUNCH();
   if (ix.nnz) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix.nnz, 256), (int64_t)num_sms() * 16));
@@ -254,14 +254,18 @@ double residual_dev(bm_ctx& h) {
   return f;
 }
 
-void line_search_coeffs_dev(bm_ctx& h, double c[5]) {
+namespace {
+// The line-search pass: per-segment sums of r b, b^2 + 2 r c, b c, c^2.
+// Returns the segment count of the split it used.
+int64_t ls_pass(bm_ctx& h) {
   const Index& ix = h.ix;
+  const Segs& sg = pass_segs(ix, kPassLsCsr);
   PipeArgs a{};
-  a.seg_row = ix.rs.row.get();
-  a.seg_beg = ix.rs.beg.get();
-  a.seg_end = ix.rs.end.get();
-  a.seg_slot = ix.rs.slot.get();
-  a.nseg = ix.rs.nseg;
+  a.seg_row = sg.row.get();
+  a.seg_beg = sg.beg.get();
+  a.seg_end = sg.end.get();
+  a.seg_slot = sg.slot.get();
+  a.nseg = sg.nseg;
   a.idx = ix.col.get();
   a.scal = h.r_csr.get();
   a.o0 = h.W.get();
@@ -280,8 +284,21 @@ void line_search_coeffs_dev(bm_ctx& h, double c[5]) {
     a.ldb = h.ldb;
   }
   BM_LAUNCH(h, bf ? "linesearch_csr_bf16" : "linesearch_csr", launch_pipe<2>(a, h.stream, bf));
+  return sg.nseg;
+}
+}  // namespace
+
+void tuning_pass_dev(bm_ctx& h, int kind) {
+  if (kind == kPassGradCsr) run_pass(h, true, false, h.sc.fseg.get());
+  else if (kind == kPassGradCsc) run_pass(h, false, false, nullptr);
+  else if (kind == kPassLsCsr) ls_pass(h);
+}
+
+void line_search_coeffs_dev(bm_ctx& h, double c[5]) {
+  const Index& ix = h.ix;
+  const int64_t nseg = ls_pass(h);
   for (int q = 0; q < 4; ++q) {
-    k_sum_double<<<1, 1024, 0, h.stream>>>(a.fseg, ix.rs.nseg, 4, q, h.sc.scal.get() + 2 + q);
+    k_sum_double<<<1, 1024, 0, h.stream>>>(h.sc.fseg.get(), nseg, 4, q, h.sc.scal.get() + 2 + q);
     BM_CHECK_LAUNCH();
   }
   double sums[4];

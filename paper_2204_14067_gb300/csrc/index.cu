@@ -296,28 +296,69 @@ int grid_for(int64_t n, int threads) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), 4 * 152 * 8));
 }
 
-void build_segs(Segs& s, const DevBuf<int64_t>& ptr_d, int64_t rows, cudaStream_t st) {
-  std::vector<int64_t> ptr(rows + 1);
-  BM_CUDA(cudaMemcpyAsync(ptr.data(), ptr_d.get(), (rows + 1) * sizeof(int64_t),
-                          cudaMemcpyDeviceToHost, st));
-  BM_CUDA(cudaStreamSynchronize(st));
+// bounds[i * (P + 1) + p] = first entry of row i whose index is >= p * pw
+// (p = 0: the row start, p = P: the row end).
+__global__ void k_panel_bounds(const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx, int64_t rows,
+                               int P, int64_t pw, int64_t* __restrict__ bounds) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rows * (P + 1);
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / (P + 1);
+    const int p = (int)(t - i * (P + 1));
+    int64_t lo = ptr[i], hi = ptr[i + 1];
+    if (p == P) {
+      bounds[t] = hi;
+      continue;
+    }
+    const int64_t target = (int64_t)p * pw;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)idx[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    bounds[t] = lo;
+  }
+}
+
+// Segments of at most kSegNnz entries within each (row, panel) piece,
+// emitted panel by panel, rows in order within a panel.  A row with no
+// entries gets one empty segment (its output is written all the same); a row
+// with several segments owns consecutive partial slots in entry order.
+void build_segs_from_bounds(Segs& s, const std::vector<int64_t>& bnd, int64_t rows, int P, cudaStream_t st) {
+  const int W = P + 1;
+  std::vector<int32_t> cnt(rows), first(rows, -1), used(rows, 0);
   std::vector<int32_t> srow, sslot, mrow, mfirst, mcount;
   std::vector<int64_t> sbeg, send;
-  int32_t nslots = 0;
+  int64_t nslots = 0;
   for (int64_t i = 0; i < rows; ++i) {
-    int64_t b = ptr[i], e = ptr[i + 1];
-    int64_t cnt = std::max<int64_t>(1, ceil_div(e - b, kSegNnz));
-    if (cnt > 1) {
+    int64_t c = 0;
+    for (int p = 0; p < P; ++p) c += ceil_div(bnd[i * W + p + 1] - bnd[i * W + p], kSegNnz);
+    cnt[i] = (int32_t)std::max<int64_t>(1, c);
+    if (cnt[i] > 1) {
+      first[i] = (int32_t)nslots;
       mrow.push_back((int32_t)i);
-      mfirst.push_back(nslots);
-      mcount.push_back((int32_t)cnt);
+      mfirst.push_back((int32_t)nslots);
+      mcount.push_back(cnt[i]);
+      nslots += cnt[i];
     }
-    for (int64_t t = 0; t < cnt; ++t) {
-      srow.push_back((int32_t)i);
-      int64_t sb = b + t * kSegNnz;
-      sbeg.push_back(sb);
-      send.push_back(std::min(e, sb + kSegNnz));
-      sslot.push_back(cnt > 1 ? nslots++ : -1);
+  }
+  BM_REQUIRE(nslots < ((int64_t)1 << 31), BM_ERR_INVALID, "index: too many partial slots");
+  for (int p = 0; p < P; ++p) {
+    for (int64_t i = 0; i < rows; ++i) {
+      const int64_t b = bnd[i * W + p], e = bnd[i * W + p + 1];
+      if (b == e) {
+        if (p == 0 && bnd[i * W] == bnd[i * W + P]) {  // empty row
+          srow.push_back((int32_t)i);
+          sbeg.push_back(b);
+          send.push_back(b);
+          sslot.push_back(-1);
+        }
+        continue;
+      }
+      for (int64_t sb = b; sb < e; sb += kSegNnz) {
+        srow.push_back((int32_t)i);
+        sbeg.push_back(sb);
+        send.push_back(std::min(e, sb + kSegNnz));
+        sslot.push_back(cnt[i] > 1 ? first[i] + used[i]++ : -1);
+      }
     }
   }
   s.nseg = (int64_t)srow.size();
@@ -340,6 +381,16 @@ void build_segs(Segs& s, const DevBuf<int64_t>& ptr_d, int64_t rows, cudaStream_
     BM_CUDA(cudaMemcpyAsync(s.mcount.get(), mcount.data(), s.nmulti * 4, cudaMemcpyHostToDevice, st));
   }
   BM_CUDA(cudaStreamSynchronize(st));
+}
+
+void build_segs(Segs& s, const DevBuf<int64_t>& ptr_d, int64_t rows, cudaStream_t st) {
+  std::vector<int64_t> ptr(rows + 1);
+  BM_CUDA(cudaMemcpyAsync(ptr.data(), ptr_d.get(), (rows + 1) * sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, st));
+  BM_CUDA(cudaStreamSynchronize(st));
+  std::vector<int64_t> bnd(2 * rows);
+  for (int64_t i = 0; i < rows; ++i) bnd[2 * i] = ptr[i], bnd[2 * i + 1] = ptr[i + 1];
+  build_segs_from_bounds(s, bnd, rows, 1, st);
 }
 
 int bits_for(uint64_t v) {  // number of bits to represent values < v
@@ -435,4 +486,52 @@ void lower_bounds_ext(const uint64_t* keys, int64_t nnz, uint64_t stride, int64_
   BM_CHECK_LAUNCH();
 }
 int key_bits_ext(uint64_t v) { return bits_for(v); }
+
+void ensure_panel_segs(bm_ctx& h, bool csr, int P) {
+  Index& ix = h.ix;
+  auto& mp = csr ? ix.rsp : ix.csp;
+  if (P <= 1 || mp.count(P)) return;
+  const int64_t rows = csr ? ix.m : ix.n, other = csr ? ix.n : ix.m;
+  const int64_t pw = ceil_div(std::max<int64_t>(other, 1), P);
+  DevBuf<int64_t> bd;
+  bd.alloc(rows * (P + 1));
+  k_panel_bounds<<<grid_for(rows * (P + 1), 256), 256, 0, h.stream>>>(
+      csr ? ix.row_ptr.get() : ix.col_ptr.get(), csr ? ix.col.get() : ix.row.get(), rows, P, pw, bd.get());
+  BM_CHECK_LAUNCH();
+  std::vector<int64_t> bnd(rows * (P + 1));
+  BM_CUDA(cudaMemcpyAsync(bnd.data(), bd.get(), bnd.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, h.stream));
+  BM_CUDA(cudaStreamSynchronize(h.stream));
+  std::unique_ptr<Segs> s(new Segs());
+  build_segs_from_bounds(*s, bnd, rows, P, h.stream);
+  mp[P] = std::move(s);
+  ensure_pass_scratch(h, 0);
+}
+
+int64_t max_slots(const Index& ix) {
+  int64_t s = std::max(ix.rs.nslots, ix.cs.nslots);
+  for (const auto& kv : ix.rsp) s = std::max(s, kv.second->nslots);
+  for (const auto& kv : ix.csp) s = std::max(s, kv.second->nslots);
+  return s;
+}
+
+int64_t max_segs(const Index& ix) {
+  int64_t s = std::max(ix.rs.nseg, ix.cs.nseg);
+  for (const auto& kv : ix.rsp) s = std::max(s, kv.second->nseg);
+  for (const auto& kv : ix.csp) s = std::max(s, kv.second->nseg);
+  return s;
+}
+
+void ensure_pass_scratch(bm_ctx& h, int ld_part) {
+  h.sc.ld_part = std::max({h.sc.ld_part, ld_part, h.ldmax});
+  const int64_t need_p = std::max<int64_t>(1, max_slots(h.ix)) * h.sc.ld_part;
+  if ((int64_t)h.sc.partial.n < need_p) {
+    h.sc.partial.release();
+    h.sc.partial.alloc(need_p);
+  }
+  const int64_t need_f = max_segs(h.ix) * 4 + 4;
+  if ((int64_t)h.sc.fseg.n < need_f) {
+    h.sc.fseg.release();
+    h.sc.fseg.alloc(need_f);
+  }
+}
 }  // namespace bm

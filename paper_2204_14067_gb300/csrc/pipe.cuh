@@ -414,8 +414,9 @@ __device__ __forceinline__ float4 gather4(const float* g, const void* gb, int64_
   return __ldg(reinterpret_cast<const float4*>(g + j * ld) + c);
 }
 
-// One segment s of a pass (the warp's lanes cooperate).
-template <int MODE, int V, bool BF>
+// One segment s of a pass (the warp's lanes cooperate).  EX: the row width is
+// exactly 4 V chunks of 4 floats, so no chunk needs a bounds test.
+template <int MODE, int V, bool BF, bool EX>
 __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
@@ -426,7 +427,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int c = l + 4 * v;
-    const bool in = c < nch;
+    const bool in = (EX || c < nch);
     w[v] = (MODE != 1 && in) ? __ldg(reinterpret_cast<const float4*>(a.o0 + (int64_t)i * a.ld) + c)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
     dw[v] = (MODE == 2 && in) ? __ldg(reinterpret_cast<const float4*>(a.o1 + (int64_t)i * a.ld) + c)
@@ -451,7 +452,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int c = l + 4 * v;
-          hv[v] = c < nch ? gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          hv[v] = (EX || c < nch) ? gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c) : make_float4(0.f, 0.f, 0.f, 0.f);
           d = fmaf(w[v].x, hv[v].x, fmaf(w[v].y, hv[v].y, fmaf(w[v].z, hv[v].z, fmaf(w[v].w, hv[v].w, d))));
         }
         d += __shfl_xor_sync(FULL, d, 1);
@@ -473,7 +474,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int c = l + 4 * v;
-          if (c < nch) {
+          if ((EX || c < nch)) {
             const float4 x = gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c);
             acc[v].x = fmaf(vv, x.x, acc[v].x);
             acc[v].y = fmaf(vv, x.y, acc[v].y);
@@ -486,7 +487,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int c = l + 4 * v;
-          if (c < nch) {
+          if ((EX || c < nch)) {
             const float4 h = gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c);
             const float4 dh = gather4<BF>(a.g1, a.g1b, jj, a.ld, a.ldb, c);
             b = fmaf(dw[v].x, h.x, fmaf(dw[v].y, h.y, fmaf(dw[v].z, h.z, fmaf(dw[v].w, h.w, b))));
@@ -523,7 +524,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const int c = l + 4 * v;
-        if (c < nch) {
+        if ((EX || c < nch)) {
           if (slot < 0) {
             float4* op = reinterpret_cast<float4*>(a.out + (int64_t)i * a.ld_out + 4 * c);
             float4 o;
@@ -569,17 +570,17 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
   }
 }
 
-template <int MODE, int V, bool BF>
+template <int MODE, int V, bool BF, bool EX>
 __global__ void __launch_bounds__(256, 3) k_direct(PipeArgs a) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < a.nseg; s += nwarps)
-    direct_segment<MODE, V, BF>(a, s);
+    direct_segment<MODE, V, BF, EX>(a, s);
 }
 
 // The same pass over several problems in one launch: segment sg of the
 // concatenated segment lists belongs to problem p with
 // prefix[p] <= sg < prefix[p + 1].
-template <int MODE, int V, bool BF>
+template <int MODE, int V, bool BF, bool EX>
 __global__ void __launch_bounds__(256, 3) k_direct_batch(const PipeArgs* __restrict__ args,
                                                          const int64_t* __restrict__ prefix, int count) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(256, 3) k_direct_batch(const PipeArgs* __restr
       const int mid = (lo + hi) >> 1;
       if (prefix[mid] <= sg) lo = mid; else hi = mid;
     }
-    direct_segment<MODE, V, BF>(args[lo], sg - prefix[lo]);
+    direct_segment<MODE, V, BF, EX>(args[lo], sg - prefix[lo]);
   }
 }
 
@@ -602,10 +603,16 @@ void launch_direct_batch(const PipeArgs* args_d, const int64_t* prefix_d, int co
   const int V = (nchunk + 3) / 4;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(total_segs, 1), 8),
                                                                (int64_t)num_sms() * 24));
-#define BM_DBATCH_CASE(VV)                                                                   \
-  case VV:                                                                                   \
-    if (bf) k_direct_batch<MODE, VV, true><<<grid, 256, 0, st>>>(args_d, prefix_d, count);   \
-    else k_direct_batch<MODE, VV, false><<<grid, 256, 0, st>>>(args_d, prefix_d, count);     \
+  const bool ex = nchunk == 4 * V;
+#define BM_DBATCH_CASE(VV)                                                                          \
+  case VV:                                                                                          \
+    if (bf) {                                                                                       \
+      if (ex) k_direct_batch<MODE, VV, true, true><<<grid, 256, 0, st>>>(args_d, prefix_d, count);  \
+      else k_direct_batch<MODE, VV, true, false><<<grid, 256, 0, st>>>(args_d, prefix_d, count);    \
+    } else {                                                                                        \
+      if (ex) k_direct_batch<MODE, VV, false, true><<<grid, 256, 0, st>>>(args_d, prefix_d, count); \
+      else k_direct_batch<MODE, VV, false, false><<<grid, 256, 0, st>>>(args_d, prefix_d, count);   \
+    }                                                                                               \
     break;
   switch (V) {
     BM_DBATCH_CASE(1)
@@ -640,10 +647,16 @@ void launch_pipe(const PipeArgs& a, cudaStream_t st, bool bf = false) {
   if (!use_pipe_kernel()) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(a.nseg, 1), 8),
                                                                  (int64_t)num_sms() * 24));
+    const bool ex = a.nchunk == 4 * V;
 #define BM_DIRECT_CASE(VV)                                                  \
   case VV:                                                                  \
-    if (bf) k_direct<MODE, VV, true><<<grid, 256, 0, st>>>(a);              \
-    else k_direct<MODE, VV, false><<<grid, 256, 0, st>>>(a);                \
+    if (bf) {                                                               \
+      if (ex) k_direct<MODE, VV, true, true><<<grid, 256, 0, st>>>(a);      \
+      else k_direct<MODE, VV, true, false><<<grid, 256, 0, st>>>(a);        \
+    } else {                                                                \
+      if (ex) k_direct<MODE, VV, false, true><<<grid, 256, 0, st>>>(a);     \
+      else k_direct<MODE, VV, false, false><<<grid, 256, 0, st>>>(a);       \
+    }                                                                       \
     return;
     switch (V) {
       BM_DIRECT_CASE(1)

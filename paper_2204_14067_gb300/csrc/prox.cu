@@ -23,7 +23,9 @@ struct ProxState {
   int ldq2 = 4;   // ld of m-side blocks (up to 2 qcap columns)
   DenseWork dw;
   DevBuf<float> mbuf[17];   // m-side blocks
-  DevBuf<float> Y, Bt;      // n-side blocks
+  DevBuf<float> Y, Bt;      // n-side blocks (ld ldq): L-application scratch, Z^T U^
+  DevBuf<float> YB;         // Z^T B_0 of the newest LmSVD block (ld ldq)
+  DevBuf<float> YQ;         // Z^T Q of the Rayleigh-Ritz basis (ld ldq2)
   DevBuf<double> G, E, ev, S1, S2;
   DevBuf<float> Ts;
   // safeguard / warm-start state
@@ -88,19 +90,25 @@ void apply_zt(bm_ctx& h, const Tall& X, const Tall& Y, double alpha) {
   spmm_dev(h, false, h.r_csc.get(), X, Y, (float)-alpha);
 }
 
-// out = Z Z^T X  (L of Eq. "ssi")
-void apply_L(bm_ctx& h, const Tall& X, const Tall& out, double alpha) {
+// out = Z Y = W (H^T Y) - alpha R Y  (Eq. "ZZ", the product with Z)
+void apply_z(bm_ctx& h, const Tall& Y, const Tall& out, double alpha) {
   ProxState& ps = *h.ps;
-  Tall Y = nview(h, ps.Y, X.cols);
-  apply_zt(h, X, Y, alpha);
   if (h.k > 0) {
     gram_dev(h, ps.dw, Hview(h), Y, ps.G.get(), false, "gram_HtY");
-    small_to_f32_dev(h, ps.G.get(), h.k, X.cols, X.cols, ps.Ts.get(), ps.ldq2);
+    small_to_f32_dev(h, ps.G.get(), h.k, Y.cols, Y.cols, ps.Ts.get(), ps.ldq2);
     gemm_dev(h, Wview(h), ps.Ts.get(), ps.ldq2, out, 0.f, 1.f, "gemm_W");
   } else {
     zero_dev(h, out);
   }
   spmm_dev(h, true, h.r_csr.get(), Y, out, (float)-alpha);
+}
+
+// out = Z Z^T X  (L of Eq. "ssi")
+void apply_L(bm_ctx& h, const Tall& X, const Tall& out, double alpha) {
+  ProxState& ps = *h.ps;
+  Tall Y = nview(h, ps.Y, X.cols);
+  apply_zt(h, X, Y, alpha);
+  apply_z(h, Y, out, alpha);
 }
 
 // Orthonormal new columns for ran([F, M]) by Eq. "PUi"/"orth-W" (two passes).
@@ -142,7 +150,7 @@ int orth_dev(bm_ctx& h, const Tall& M, const Tall* F, const Tall* LM, const Tall
     int c2 = c1;
     if (pass == 0) {
       // Eq. "orth-W": eigen-decomposition of P^T P, drop eigenvalues <= tau, scale by Lambda^{-1/2}
-      sym_eig_dev(h, ps.dw, ps.G.get(), c1, ps.ev.get(), ps.E.get(), false);
+      sym_eig_dev(h, ps.dw, ps.G.get(), c1, ps.ev.get(), ps.E.get(), kEigFast);
       std::vector<double> lam = to_host(h, ps.ev.get(), c1);
       std::vector<int> keep;
       std::vector<double> s;
@@ -201,17 +209,29 @@ struct LmsvdOut {
   std::vector<double> theta;
 };
 
-// LmSVD (Algorithm 2) from the warm start in block kUw (c0 columns); result in kU.
+// LmSVD (Algorithm 2) from the warm start in block kUw (c0 columns).  Result:
+// the Ritz vectors U^ in kU and their images Z^T U^ in ps.Bt.
+//
+// The subspace is the paper's: Q = [B_0, orth(B_1 | B_0)] with B_0 =
+// orth(L(U^)) the newest block and B_1 the previous one (memory p = 1).  The
+// Rayleigh-Ritz matrix Q^T L Q is formed as (Z^T Q)^T (Z^T Q) from images
+// Z^T B_0 (kept from the block's creation) and Z^T Q_2 of the new directions,
+// and L(U^) as Z (Z^T U^): in FP32 the product L = Z Z^T carries errors of
+// order eps * sigma_1^2 into every column, which would swamp the small
+// singular values near the threshold lambda * alpha, while products with Z
+// and Z^T alone err by eps * sigma_1 * (size of the column).  The small
+// eigenproblem runs in the relative-accuracy mode for the same reason.
 LmsvdOut lmsvd_dev(bm_ctx& h, int c0, double alpha) {
   ProxState& ps = *h.ps;
   const bm_options& o = h.opt;
+  const int64_t n = h.ix.n;
   LmsvdOut r{0, 0, 0, {}};
-  int B[3] = {kB0, kB1, kB2}, LB[3] = {kLB0, kLB1, kLB2};
+  int B[3] = {kB0, kB1, kB2};
   int kc[3] = {0, 0, 0};
   const int k0 = orth_dev(h, mview(h, kUw, c0), nullptr, nullptr, nullptr, o.tau, -1, B[0], 0, -1);
   if (k0 == 0) return r;
   kc[0] = k0;
-  apply_L(h, mview(h, B[0], k0), mview(h, LB[0], k0), alpha);
+  apply_zt(h, mview(h, B[0], k0), nview(h, ps.YB, k0), alpha);   // Z^T B_0
   r.nL = 1;
   int nb = 1;
   const int k = k0;
@@ -219,27 +239,33 @@ LmsvdOut lmsvd_dev(bm_ctx& h, int c0, double alpha) {
   for (int it = 1; it <= o.lmsvd_imax; ++it) {
     r.iters = it;
     int q = kc[0];
-    Tall Q = mview(h, B[0], kc[0]), LQ = mview(h, LB[0], kc[0]);
+    Tall Q = mview(h, B[0], kc[0]);
+    copy_cols_dev(h, nview(h, ps.YB, kc[0]), 0, Tall{ps.YQ.get(), n, kc[0], ps.ldq2}, 0, kc[0]);
     if (nb > 1) {
       copy_cols_dev(h, mview(h, B[0], kc[0]), 0, mview(h, kQ, kc[0]), 0, kc[0]);
-      copy_cols_dev(h, mview(h, LB[0], kc[0]), 0, mview(h, kLQ, kc[0]), 0, kc[0]);
-      Tall F = mview(h, B[0], kc[0]), LF = mview(h, LB[0], kc[0]);
-      Tall Mo = mview(h, B[1], kc[1]), LMo = mview(h, LB[1], kc[1]);
-      const int c2 = orth_dev(h, Mo, &F, &LMo, &LF, o.tau, -1, kQ, kc[0], kLQ);
+      Tall F = mview(h, B[0], kc[0]);
+      const int c2 = orth_dev(h, mview(h, B[1], kc[1]), &F, nullptr, nullptr, o.tau, -1, kLQ, 0, -1);
+      if (c2 > 0) {
+        const Tall Q2 = mview(h, kLQ, c2);
+        apply_zt(h, Q2, nview(h, ps.Y, c2), alpha);                  // Z^T Q_2
+        r.nL += 1;
+        copy_cols_dev(h, Q2, 0, mview(h, kQ, kc[0] + c2), kc[0], c2);
+        copy_cols_dev(h, nview(h, ps.Y, c2), 0, Tall{ps.YQ.get(), n, kc[0] + c2, ps.ldq2}, kc[0], c2);
+      }
       q = kc[0] + c2;
       Q = mview(h, kQ, q);
-      LQ = mview(h, kLQ, q);
     }
-    gram_dev(h, ps.dw, Q, LQ, ps.G.get(), true, "gram_rr");
-    sym_eig_dev(h, ps.dw, ps.G.get(), q, ps.ev.get(), ps.E.get(), false);  // FP32 Rayleigh-Ritz
+    const Tall YQ{ps.YQ.get(), n, q, ps.ldq2};
+    gram_dev(h, ps.dw, YQ, YQ, ps.G.get(), false, "gram_rr");           // Q^T L Q
+    sym_eig_dev(h, ps.dw, ps.G.get(), q, ps.ev.get(), ps.E.get(), kEigRelative);
     std::vector<double> th = to_host(h, ps.ev.get(), q);
     const int kk = std::min(k, q);
     std::vector<int> sel(kk);
     std::vector<double> one(kk, 1.0);
     for (int j = 0; j < kk; ++j) sel[j] = j;
     make_transform(h, ps.E.get(), q, q, sel, one);
-    gemm_dev(h, Q, ps.Ts.get(), ps.ldq2, mview(h, kU, kk), 0.f, 1.f, "gemm_rr");
-    gemm_dev(h, LQ, ps.Ts.get(), ps.ldq2, mview(h, kX3, kk), 0.f, 1.f, "gemm_rr");  // L(U^)
+    gemm_dev(h, Q, ps.Ts.get(), ps.ldq2, mview(h, kU, kk), 0.f, 1.f, "gemm_rr");      // U^
+    gemm_dev(h, YQ, ps.Ts.get(), ps.ldq2, nview(h, ps.Bt, kk), 0.f, 1.f, "gemm_rr_y");  // Z^T U^
     th.resize(kk);
     r.cols = kk;
     r.theta = th;
@@ -251,23 +277,18 @@ LmsvdOut lmsvd_dev(bm_ctx& h, int c0, double alpha) {
     }
     if (conv || it == o.lmsvd_imax) break;
     theta_prev = th;
-    // next block U^{t,i+1} = orth(L(U^)) into the free slot
-    int fb = B[2], flb = LB[2];
-    // move L(U^) out of X3 (orth uses X1..X4 as work space)
-    copy_cols_dev(h, mview(h, kX3, kk), 0, mview(h, kQ, kk), 0, kk);
-    const int cn = orth_dev(h, mview(h, kQ, kk), nullptr, nullptr, nullptr, o.tau, -1, fb, 0, -1);
+    // next block U^{t,i+1} = orth(L(U^)), L(U^) = Z (Z^T U^)
+    apply_z(h, nview(h, ps.Bt, kk), mview(h, kLB0, kk), alpha);
+    const int fb = B[2];
+    const int cn = orth_dev(h, mview(h, kLB0, kk), nullptr, nullptr, nullptr, o.tau, -1, fb, 0, -1);
     if (cn == 0) break;
-    apply_L(h, mview(h, fb, cn), mview(h, flb, cn), alpha);
+    apply_zt(h, mview(h, fb, cn), nview(h, ps.YB, cn), alpha);         // Z^T B_new
     r.nL += 1;
     // rotate: new block first, keep p older ones
-    const int ob = B[0], olb = LB[0], okc = kc[0];
     B[2] = B[1];
-    LB[2] = LB[1];
-    B[1] = ob;
-    LB[1] = olb;
-    kc[1] = okc;
+    B[1] = B[0];
+    kc[1] = kc[0];
     B[0] = fb;
-    LB[0] = flb;
     kc[0] = cn;
     nb = std::min(nb + 1, o.lmsvd_p + 1);
   }
@@ -283,7 +304,7 @@ struct SvtOut {
 };
 
 // Exact SVD of U^T Z, soft-threshold, refactor.  U^ in kU (kf columns).
-SvtOut svt_refactor_dev(bm_ctx& h, int kf, double thresh, double alpha, double frob2) {
+SvtOut svt_refactor_dev(bm_ctx& h, int kf, double thresh, double alpha, double frob2, bool bt_ready) {
   ProxState& ps = *h.ps;
   SvtOut out{0, false, 0.0, {}, 0.0};
   const Index& ix = h.ix;
@@ -300,9 +321,9 @@ SvtOut svt_refactor_dev(bm_ctx& h, int kf, double thresh, double alpha, double f
   }
   Tall Uh = mview(h, kU, kf);
   Tall Bt = nview(h, ps.Bt, kf);
-  apply_zt(h, Uh, Bt, alpha);                                   // (U^T Z)^T
+  if (!bt_ready) apply_zt(h, Uh, Bt, alpha);                    // (U^T Z)^T
   gram_dev(h, ps.dw, Bt, Bt, ps.G.get(), true, "gram_BBt");     // B B^T
-  sym_eig_dev(h, ps.dw, ps.G.get(), kf, ps.ev.get(), ps.E.get(), true);
+  sym_eig_dev(h, ps.dw, ps.G.get(), kf, ps.ev.get(), ps.E.get(), kEigRelative);
   std::vector<double> s2 = to_host(h, ps.ev.get(), kf);
   std::vector<double> sh(kf);
   double sum_s2 = 0;
@@ -395,6 +416,8 @@ void prox_create(bm_ctx& h) {
   ps.ldq2 = round_up4(2 * ps.qcap);
   for (auto& b : ps.mbuf) b.alloc((size_t)h.ix.m * ps.ldq2);
   ps.Y.alloc((size_t)h.ix.n * ps.ldq);
+  ps.YB.alloc((size_t)h.ix.n * ps.ldq);
+  ps.YQ.alloc((size_t)h.ix.n * ps.ldq2);
 
   ps.Bt.alloc((size_t)h.ix.n * ps.ldq);
   const size_t q2 = (size_t)2 * ps.qcap;
@@ -405,11 +428,7 @@ void prox_create(bm_ctx& h) {
   ps.S2.alloc(q2 * q2);
   ps.Ts.alloc(q2 * ps.ldq2);
   // q-wide SpMM partials need nslots x round_up4(qcap)
-  const int64_t slots = std::max<int64_t>(1, std::max(h.ix.rs.nslots, h.ix.cs.nslots));
-  if ((int64_t)h.sc.partial.n < slots * ps.ldq) {
-    h.sc.partial.release();
-    h.sc.partial.alloc(slots * ps.ldq);
-  }
+  ensure_pass_scratch(h, ps.ldq);
   ps.psi = h.opt.psi0;
 }
 
@@ -502,7 +521,7 @@ void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info) {
       while (kf < l.cols && std::sqrt(std::max(l.theta[kf], 0.0)) > o.ritz_rel * s1) ++kf;
     }
   }
-  SvtOut s = svt_refactor_dev(h, kf, h.lambda * alpha, alpha, frob2);
+  SvtOut s = svt_refactor_dev(h, kf, h.lambda * alpha, alpha, frob2, kf > 0);
   // ---- safeguard bookkeeping
   if (s.k_new == warm - 1) ps.psi *= 0.5;
   ps.rank_prev = ps.rank_cur;
@@ -537,7 +556,7 @@ void init_step_dev(bm_ctx& h, bm_prox_info* info) {
     apply_L(h, mview(h, kB0, cq), mview(h, kLB0, cq), alpha);                      // A Q
     l.nL = 3;
     gram_dev(h, ps.dw, mview(h, kB0, cq), mview(h, kLB0, cq), ps.S1.get(), true, "gram_rr");  // Q^T A Q
-    sym_eig_dev(h, ps.dw, ps.S1.get(), cq, ps.ev.get(), ps.E.get(), true);
+    sym_eig_dev(h, ps.dw, ps.S1.get(), cq, ps.ev.get(), ps.E.get(), kEigRelative);
     std::vector<double> cw = to_host(h, ps.ev.get(), cq);
     std::vector<double> E = to_host(h, ps.E.get(), (size_t)cq * cq);
     // (Q^T A Q)^dagger by the eigen-pseudo-inverse (cutoff tau * largest), formed on the host (cq x cq)
@@ -554,7 +573,7 @@ void init_step_dev(bm_ctx& h, bm_prox_info* info) {
       // M = R^ P R^^T  (cqh x cqh)
       small_mm_dev(h, ps.S1.get(), ps.S2.get(), ps.E.get(), cqh, cq, cq, false);
       small_mm_dev(h, ps.E.get(), ps.S1.get(), ps.G.get(), cqh, cq, cqh, true);
-      sym_eig_dev(h, ps.dw, ps.G.get(), cqh, ps.ev.get(), ps.E.get(), true);
+      sym_eig_dev(h, ps.dw, ps.G.get(), cqh, ps.ev.get(), ps.E.get(), kEigRelative);
       std::vector<double> s2 = to_host(h, ps.ev.get(), cqh);
       const double s1 = std::sqrt(std::max(s2[0], 0.0));
       std::vector<int> sel;
@@ -572,7 +591,7 @@ void init_step_dev(bm_ctx& h, bm_prox_info* info) {
   ps.initialized = true;
   ps.ku = 0;
   ps.ku2 = -1;
-  SvtOut s = svt_refactor_dev(h, kf, h.lambda * alpha, alpha, frob2);
+  SvtOut s = svt_refactor_dev(h, kf, h.lambda * alpha, alpha, frob2, false);
   ps.ku2 = -1;
   ps.psi = o.psi0;
   ps.rank_prev = 0;
@@ -582,6 +601,19 @@ void init_step_dev(bm_ctx& h, bm_prox_info* info) {
   h.bm_changed = false;
   const double F = info ? objective_ext(h) : 0.0;
   fill_info(info, s, kf, l, F);
+}
+
+}  // namespace bm
+
+namespace bm {
+
+void tuning_spmm_dev(bm_ctx& h, bool csr) {
+  ProxState& ps = *h.ps;
+  const int q = std::max(1, std::min(ps.qcap, h.k + 1));
+  const Tall mside = mview(h, kX1, q);
+  const Tall nside = nview(h, ps.Y, q);
+  if (csr) spmm_dev(h, true, h.r_csr.get(), nside, mside, -1.f);
+  else spmm_dev(h, false, h.r_csc.get(), mside, nside, -1.f);
 }
 
 }  // namespace bm

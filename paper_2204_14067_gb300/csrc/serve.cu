@@ -74,7 +74,7 @@ size_t estimate_bytes(const Request& r, int prec) {
   size_t b = (size_t)nnz * (4 + 4 + 4 + 4 + 8 + 4 + 4 + 4);       // index, map, residual in both orders
   b += (size_t)nnz * 24;                                          // radix-sort scratch during create
   b += (size_t)(m + n) * ld * 4 * 8;                               // W, H, gradients, directions
-  b += (size_t)m * ld2 * 4 * 17 + (size_t)n * ld * 4 * 2;          // PG blocks
+  b += (size_t)m * ld2 * 4 * 17 + (size_t)n * ld * 4 * 3 + (size_t)n * ld2 * 4;  // PG blocks
   if (prec == 1) b += (size_t)(m + n) * ld * 2 * 3 + (size_t)std::max(m * ld2, n * ld) * 2;
   return b + b / 4 + (64u << 20);
 }

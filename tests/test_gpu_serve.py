@@ -19,8 +19,10 @@ def B():
 
 
 def _requests(count=10, seed=9):
+    # lambda in {3, 5, 8} max|A|: optimum ranks 3..29 under the cap of 32, so
+    # every request has a unique optimal objective that both modes must reach
     return serving_requests(count=count, seed=seed, m_range=(500, 6000), n_range=(300, 3000),
-                            density_range=(0.005, 0.03), rate=200.0, k_max=16)
+                            density_range=(0.005, 0.03), rate=200.0, k_max=32, lam_grid=(3.0, 5.0, 8.0))
 
 
 def _serve(B, probs, arrivals, **kw):
@@ -57,4 +59,5 @@ def test_server_alone_equals_mix_and_modes_agree(B):
                 max_outer=400, tol=1e-8)
     for a, b in zip(plain, bf):
         assert a["status"] == 0 and b["status"] == 0
+        assert a["k"] < 32 and b["k"] < 32
         assert abs(a["F"] - b["F"]) <= 1e-4 * abs(a["F"]), (a, b)
