@@ -8,6 +8,8 @@ soft-threshold, refactor).  `value` counts observed entries processed per
 second per cycle (nnz / cycle time) summed over replicas.
 
 `--mode grad` times bm_loss_grad alone (the SDDMM + two SpMM passes).
+`--mode tto` times a solve to the FP64 oracle's objective on the planted
+500 x 300 problem; `--mode serve` measures the continuous-batching server.
 `--impl reference` times the FP64 oracle on the host cores on a bounded
 sample of the same workload.
 """
@@ -399,6 +401,121 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _read_golden_tiny():
+    vals = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "tiny_optimum.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()
+        vals[k] = float(v)
+    return vals["F_star"], int(vals["rank"])
+
+
+def run_tto(args):
+    """Time to the oracle's objective: wall time of bm_solve from X = 0 until
+    F <= F*(1 + 1e-6) on the 500 x 300 planted problem, F* being the FP64
+    oracle's converged objective (tests/golden/tiny_optimum.txt)."""
+    import torch
+
+    import paper_2204_14067_gb300 as B
+    from synth import named_config
+
+    F_star, rank = _read_golden_tiny()
+    p = named_config("tiny")
+    target = F_star * (1 + 1e-6)
+    runs = []
+    for rep in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 64)
+        t1 = time.perf_counter()
+        r = B.bm_solve(h, max_outer=2000, tol=0.0, F_target=target)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        B.bm_get_factors(h, p.m, p.n)
+        t3 = time.perf_counter()
+        B.bm_destroy(h)
+        if rep >= args.warmup:
+            runs.append((t2 - t1, t3 - t0, r["outer"], r["F"], bool(r["converged"])))
+    solve_s = statistics.median(x[0] for x in runs)
+    e2e_s = statistics.median(x[1] for x in runs)
+    cpu = None
+    if not args.no_cpu:
+        from oracle import bm_oracle as O
+        ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
+        t0 = time.perf_counter()
+        _, oi = O.solve(ix, p.lam, 8, 64, O.Options(), max_outer=2000, tol=0.0, F_target=target)
+        cpu = {"value": time.perf_counter() - t0, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"the same solve to the same target ({oi.outer} cycles)"}
+    return {
+        "metric": "time to oracle objective (relative 1e-6)", "value": solve_s, "unit": "s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "planted rank-5 500x300, 15,000 entries, lambda 0.5, k0 8, k_max 64",
+                   "F_star": F_star, "oracle_rank": rank, "cycles": [x[2] for x in runs],
+                   "converged": all(x[4] for x in runs), "final_rel": max((x[3] - F_star) / F_star for x in runs)},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(p.nnz * 12),
+                "d2h_bytes_per_step": int((p.m + p.n) * 64 * 4)},
+        "cpu_baseline": cpu,
+    }
+
+
+def run_serve(args):
+    """Continuous-batching serving on a bounded sample of the request stream:
+    capacity of one-at-a-time FP32 solves, then Poisson arrivals at 0.8 of it
+    served by the batched BF16 server and by the one-at-a-time FP32 server."""
+    import torch
+
+    import paper_2204_14067_gb300 as B
+    from synth import serving_requests
+
+    count = args.serve_count
+    probs, _ = serving_requests(count=count, seed=4, max_nnz=4_000_000, k_max=32)
+    torch.cuda.synchronize()
+
+    def serve(arrivals, **kw):
+        s = B.bm_server_create(max_outer=100, tol=1e-7, **kw)
+        try:
+            t0 = time.perf_counter()
+            ids = []
+            for q, t in zip(probs, arrivals):
+                d = t - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                ids.append(B.bm_server_submit(s, q.m, q.n, q.rows, q.cols, q.vals, q.lam, q.k_max))
+            B.bm_server_drain(s, 3600.0)
+            wall = time.perf_counter() - t0
+            res = {r["id"]: r for r in B.bm_server_results(s)}
+            return [res[i] for i in ids], wall
+        finally:
+            B.bm_server_destroy(s)
+
+    plain0, t_cap = serve(np.zeros(count), max_active=1, precision=0, batched=0, workers=1)
+    cap = count / t_cap
+    rate = 0.8 * cap
+    rng = np.random.default_rng(123)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+    bat, wall_b = serve(arrivals, max_active=16, precision=1, batched=1, workers=8)
+    pla, wall_p = serve(arrivals, max_active=1, precision=0, batched=0, workers=1)
+
+    def stats(res, wall):
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "solves_per_s": len(res) / wall, "errors": int(sum(r["status"] != 0 for r in res))}
+
+    sb, sp = stats(bat, wall_b), stats(pla, wall_p)
+    rel = max(abs(a["F"] - b["F"]) / abs(b["F"]) for a, b in zip(bat, pla))
+    return {
+        "metric": "serving solves/s (batched BF16 + FP32 refinement)", "value": sb["solves_per_s"],
+        "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall_b * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
+        "config": {"workload": f"{count} requests: m log-U[1k,200k], n log-U[500,20k], density log-U[0.1%,2%], "
+                               "nnz <= 4M, planted rank 2..16, lambda {0.02..0.5} max|A|, k_max 32",
+                   "arrival_rate_per_s": rate, "fp32_capacity_per_s": cap},
+        "batched_bf16": sb, "one_at_a_time_fp32": sp, "max_rel_objective_diff": rel,
+    }
+
+
 def _dist_cpu():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return None, int(os.environ.get("RANK", "0")), ws
@@ -410,14 +527,22 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="cycle", choices=["cycle", "grad"])
+    ap.add_argument("--mode", default="cycle", choices=["cycle", "grad", "tto", "serve"])
+    ap.add_argument("--serve-count", type=int, default=48)
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the natural work split (one panel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.mode == "tto":
+        line = run_tto(args)
+    elif args.mode == "serve":
+        line = run_serve(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line))
 

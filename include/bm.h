@@ -207,6 +207,20 @@ bm_status bm_prox_step(bm_handle h, double alpha, bm_prox_info* info);
 bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info);
 
 /*
+ * Checkpoint / resume (no counterpart in the paper).  bm_get_state writes the
+ * solve state into a caller-owned host buffer: the rank, W and H, the PG
+ * step's warm-start and safeguard state (U_t, U_{t-1}, the truncated vector
+ * u, psi_t, the rank history, t) and the work-split choice; with buf = NULL
+ * it only stores the required size in *len (BM_ERR_INVALID if *len is too
+ * small).  bm_set_state restores such a state into a handle created for the
+ * same problem (same m, n, |Omega| and k_max; BM_ERR_INVALID otherwise, or
+ * for a damaged buffer).  A solve continued after bm_set_state takes the
+ * same steps as one that was never interrupted.
+ */
+bm_status bm_get_state(bm_handle h, void* buf, size_t* len);
+bm_status bm_set_state(bm_handle h, const void* buf, size_t len);
+
+/*
  * Work-split tuning of the sparse passes (no counterpart in the paper; it
  * changes the order of work, not the arithmetic of Eq. (MF) and (ZZ)).
  * Pass kinds, in array order: 0 loss/gradient over rows (gathers H), 1

@@ -552,14 +552,21 @@ class SolveInfo:
 
 
 def solve(ix: Index, lam: float, k_init: int, k_max: int, opt: Options = Options(),
-          max_outer: int = 100, tol: float = 1e-10, F_target: Optional[float] = None):
+          max_outer: int = 100, tol: float = 1e-10, F_target: Optional[float] = None,
+          state: Optional[State] = None):
     """BM-Global (Algorithm 1): initial PG step from 0, then cycles of
     `bm_epochs` BM iterations and `pg_steps` inexact PG steps; the rank is
-    the number of singular values that survive the threshold."""
-    st, info0 = init_step(ix, lam, k_init, k_max, opt)
+    the number of singular values that survive the threshold.  With `state`
+    (a State returned by an earlier call) the cycles resume from it instead
+    of the initial step."""
+    if state is None:
+        st, info0 = init_step(ix, lam, k_init, k_max, opt)
+        k0, eps0 = info0.k_new, info0.eps
+    else:
+        st, k0, eps0 = state, state.W.shape[1], float("nan")
     F_hist = [objective(ix, st.W, st.H, lam)]
-    k_hist = [info0.k_new]
-    eps_hist = [info0.eps]
+    k_hist = [k0]
+    eps_hist = [eps0]
     its = [0]
     outer = 0
     for outer in range(1, max_outer + 1):

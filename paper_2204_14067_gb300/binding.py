@@ -84,6 +84,8 @@ _SIGS = {
     "bm_solve": (_c.c_int, [_P, _c.POINTER(bm_solve_opts), _c.POINTER(bm_solve_info)]),
     "bm_profile_enable": (_c.c_int, [_P, _c.c_int32]),
     "bm_autotune": (_c.c_int, [_P, _c.c_int32, _c.POINTER(bm_tune_info)]),
+    "bm_get_state": (_c.c_int, [_P, _P, _c.POINTER(_c.c_size_t)]),
+    "bm_set_state": (_c.c_int, [_P, _P, _c.c_size_t]),
     "bm_set_panels": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_get_panels": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_profile_read": (_c.c_int, [_P, _c.c_int32, _P, _P, _P, _P]),
@@ -249,6 +251,20 @@ def bm_autotune(h, max_panels=BM_MAX_PANELS):
     _check(lib().bm_autotune(h, int(max_panels), ctypes.byref(info)), h)
     return {nm: (int(info.panels[i]), float(info.ms[i]), float(info.ms_single[i]))
             for i, nm in enumerate(PASS_NAMES)}
+
+
+def bm_get_state(h) -> bytes:
+    """Checkpoint of the solve state (host bytes)."""
+    n = ctypes.c_size_t(0)
+    _check(lib().bm_get_state(h, None, ctypes.byref(n)), h)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().bm_get_state(h, buf, ctypes.byref(n)), h)
+    return buf.raw[: n.value]
+
+
+def bm_set_state(h, state: bytes):
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(lib().bm_set_state(h, buf, len(state)), h)
 
 
 def bm_set_panels(h, panels):

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <new>
 
 #include "ctx.cuh"
@@ -372,6 +373,90 @@ bm_status bm_set_factors(bm_handle h, int32_t k, const float* W, const float* H)
     prox_reset(*h);
     h->bm_changed = true;
     BM_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+namespace {
+// Checkpoint layout: this header, W (m x k) and H (n x k) in the internal
+// orientation with rows packed, then the PG-step state.
+struct StateHeader {
+  char magic[8];
+  int64_t m, n, nnz;
+  int32_t k, k_max;
+  int32_t bm_changed, refine;
+  int32_t panels[kPassKinds];
+  int32_t pad_;
+  int64_t prox_bytes;
+};
+constexpr char kStateMagic[8] = {'B', 'M', 'S', 'T', 'A', 'T', 'E', '1'};
+}  // namespace
+
+bm_status bm_get_state(bm_handle h, void* buf, size_t* len) {
+  if (!h || !len) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    const size_t pb = prox_state_bytes(*h);
+    const size_t fb = ((size_t)h->ix.m + (size_t)h->ix.n) * (size_t)h->k * sizeof(float);
+    const size_t need = sizeof(StateHeader) + fb + pb;
+    if (!buf) {
+      *len = need;
+      return;
+    }
+    BM_REQUIRE(*len >= need, BM_ERR_INVALID, "bm_get_state: buffer too small (pass buf = NULL to get the size)");
+    StateHeader hd{};
+    std::memcpy(hd.magic, kStateMagic, sizeof(kStateMagic));
+    hd.m = h->ix.m;
+    hd.n = h->ix.n;
+    hd.nnz = h->ix.nnz;
+    hd.k = h->k;
+    hd.k_max = h->k_max;
+    hd.bm_changed = h->bm_changed ? 1 : 0;
+    hd.refine = h->refine ? 1 : 0;
+    for (int i = 0; i < kPassKinds; ++i) hd.panels[i] = h->ix.panels[i];
+    hd.prox_bytes = (int64_t)pb;
+    uint8_t* p = static_cast<uint8_t*>(buf);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    copy_out_rows(*h, reinterpret_cast<float*>(p), h->W.get(), h->ix.m, h->k);
+    p += (size_t)h->ix.m * h->k * sizeof(float);
+    copy_out_rows(*h, reinterpret_cast<float*>(p), h->H.get(), h->ix.n, h->k);
+    p += (size_t)h->ix.n * h->k * sizeof(float);
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+    prox_state_save(*h, p);
+    *len = need;
+  });
+}
+
+bm_status bm_set_state(bm_handle h, const void* buf, size_t len) {
+  if (!h || !buf) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    BM_REQUIRE(len >= sizeof(StateHeader), BM_ERR_INVALID, "bm_set_state: truncated state");
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    BM_REQUIRE(std::memcmp(hd.magic, kStateMagic, sizeof(kStateMagic)) == 0, BM_ERR_INVALID,
+               "bm_set_state: not a state written by bm_get_state");
+    BM_REQUIRE(hd.m == h->ix.m && hd.n == h->ix.n && hd.nnz == h->ix.nnz && hd.k_max == h->k_max, BM_ERR_INVALID,
+               "bm_set_state: the state belongs to a problem of other dimensions or rank cap");
+    BM_REQUIRE(hd.k >= 0 && hd.k <= h->k_max && hd.prox_bytes >= 0, BM_ERR_INVALID, "bm_set_state: invalid state");
+    for (int i = 0; i < kPassKinds; ++i)
+      BM_REQUIRE(hd.panels[i] >= 1 && hd.panels[i] <= BM_MAX_PANELS, BM_ERR_INVALID, "bm_set_state: invalid state");
+    const size_t fb = ((size_t)hd.m + (size_t)hd.n) * (size_t)hd.k * sizeof(float);
+    BM_REQUIRE(len == sizeof(StateHeader) + fb + (size_t)hd.prox_bytes, BM_ERR_INVALID,
+               "bm_set_state: state size mismatch");
+    const uint8_t* p = static_cast<const uint8_t*>(buf) + sizeof(hd);
+    set_rank(*h, hd.k);
+    copy_in_rows(*h, h->W.get(), reinterpret_cast<const float*>(p), h->ix.m, hd.k);
+    p += (size_t)hd.m * hd.k * sizeof(float);
+    copy_in_rows(*h, h->H.get(), reinterpret_cast<const float*>(p), h->ix.n, hd.k);
+    p += (size_t)hd.n * hd.k * sizeof(float);
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < kPassKinds; ++i) {
+      ensure_panel_segs(*h, pass_is_csr(i), hd.panels[i]);
+      h->ix.panels[i] = hd.panels[i];
+    }
+    prox_reset(*h);
+    prox_state_load(*h, p, (size_t)hd.prox_bytes);
+    h->bm_changed = hd.bm_changed != 0;
+    h->refine = hd.refine != 0;
   });
 }
 

@@ -118,12 +118,12 @@ struct bm_ctx {
   bm::Profiler prof;
   std::string err;
   bool bm_changed = false;       // BM phase moved since the last PG step
-  // BF16 gathers (bm_options.precision == 1): copies of W, H, D_H and of the
-  // SpMM operand, row stride ldb = round_up(ld, 8) elements, zero padded.
+  // BF16 gathers (bm_options.precision == 1): copies of W, H and D_H, row
+  // stride ldb = round_up(ld, 8) elements, zero padded.
   bool refine = false;           // bm_solve switched to FP32 for the final iterations
   bool bf_dirty = true;          // W/H changed since the copies were made
   int ldb = 8;
-  bm::DevBuf<uint16_t> Wb, Hb, DHb, Xb;
+  bm::DevBuf<uint16_t> Wb, Hb, DHb;
   bool bf_active() const { return opt.precision == 1 && !refine; }
   bool tuned = false;            // panel counts chosen (bm_autotune / bm_set_panels)
 };
@@ -205,6 +205,11 @@ void prox_destroy(bm_ctx& h);
 void prox_reset(bm_ctx& h);
 void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info);
 void init_step_dev(bm_ctx& h, bm_prox_info* info);
+// Checkpoint of the PG-step state (warm start and safeguard): size, save
+// into host memory, load from host memory (validated; BM_ERR_INVALID).
+size_t prox_state_bytes(const bm_ctx& h);
+void prox_state_save(bm_ctx& h, uint8_t* out);
+void prox_state_load(bm_ctx& h, const uint8_t* in, size_t len);
 // One q-wide SpMM of the PG step (CSR: R Y, CSC: R^T U) on scratch blocks of
 // width min(k_max + 1, k + 1), for timing.
 void tuning_spmm_dev(bm_ctx& h, bool csr);

@@ -832,42 +832,37 @@ void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall&
   const Index& ix = h.ix;
   const Segs& sg = pass_segs(ix, csr ? kPassSpmmCsr : kPassSpmmCsc);
   if (X.cols == 0) return;
-  PipeArgs a{};
-  a.seg_row = sg.row.get();
-  a.seg_beg = sg.beg.get();
-  a.seg_end = sg.end.get();
-  a.seg_slot = sg.slot.get();
-  a.nseg = sg.nseg;
-  a.idx = csr ? ix.col.get() : ix.row.get();
-  a.scal = vals;
-  a.g0 = X.p;
-  a.ld = X.ld;
-  a.nchunk = (X.cols + 3) / 4;
-  a.gamma = gamma;
-  a.out = Out.p;
-  a.ld_out = Out.ld;
-  a.partial = h.sc.partial.get();
-  a.ld_part = 4 * a.nchunk;
-  BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ld_part <= (int64_t)h.sc.partial.n, BM_ERR_INVALID,
-             "spmm: partial buffer too small");
-  // The residual products of the PG step gather FP32 rows: BF16 operands
-  // leave LmSVD short of its stop tolerance (the factor gathers of the BM
-  // phase are the ones that use BF16).
-  const bool bf = false;
-  if (bf) {
-    const int ldb = ((X.ld + 7) / 8) * 8;
-    BM_REQUIRE((size_t)X.rows * ldb <= h.Xb.n, BM_ERR_INVALID, "spmm: BF16 operand buffer too small");
-    to_bf16_dev(h, X.p, X.rows, X.ld, h.Xb.get(), ldb);
-    a.g0b = h.Xb.get();
-    a.ldb = ldb;
-  }
-  BM_LAUNCH(h, csr ? (bf ? "spmm_csr_bf16" : "spmm_csr") : (bf ? "spmm_csc_bf16" : "spmm_csc"),
-            launch_pipe<1>(a, h.stream, bf));
-  if (sg.nmulti) {
-    BM_LAUNCH(h, "spmm_fixup",
-              k_spmm_fixup<<<grid1(sg.nmulti * X.cols), 256, 0, h.stream>>>(
-                  sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti, a.partial, a.ld_part, X.cols, gamma,
-                  Out.p, Out.ld));
+  // one launch per slice of at most kSpmmCols columns (the kernel's widest row)
+  for (int c0 = 0; c0 < X.cols; c0 += kSpmmCols) {
+    const int cols = std::min(kSpmmCols, X.cols - c0);
+    PipeArgs a{};
+    a.seg_row = sg.row.get();
+    a.seg_beg = sg.beg.get();
+    a.seg_end = sg.end.get();
+    a.seg_slot = sg.slot.get();
+    a.nseg = sg.nseg;
+    a.idx = csr ? ix.col.get() : ix.row.get();
+    a.scal = vals;
+    a.g0 = X.p + c0;
+    a.ld = X.ld;
+    a.nchunk = (cols + 3) / 4;
+    a.gamma = gamma;
+    a.out = Out.p + c0;
+    a.ld_out = Out.ld;
+    a.partial = h.sc.partial.get();
+    a.ld_part = 4 * a.nchunk;
+    BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ld_part <= (int64_t)h.sc.partial.n, BM_ERR_INVALID,
+               "spmm: partial buffer too small");
+    // The residual products of the PG step gather FP32 rows: BF16 operands
+    // leave LmSVD short of its stop tolerance (the factor gathers of the BM
+    // phase are the ones that use BF16).
+    BM_LAUNCH(h, csr ? "spmm_csr" : "spmm_csc", launch_pipe<1>(a, h.stream, false));
+    if (sg.nmulti) {
+      BM_LAUNCH(h, "spmm_fixup",
+                k_spmm_fixup<<<grid1(sg.nmulti * cols), 256, 0, h.stream>>>(
+                    sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti, a.partial, a.ld_part, cols, gamma,
+                    a.out, Out.ld));
+    }
   }
 }
 

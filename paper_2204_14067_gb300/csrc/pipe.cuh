@@ -668,8 +668,16 @@ void launch_pipe(const PipeArgs& a, cudaStream_t st, bool bf = false) {
       BM_DIRECT_CASE(7)
       BM_DIRECT_CASE(8)
       default:
-        throw Error{BM_ERR_INVALID, "sparse pass: more than 128 columns"};
+        break;
     }
+    if constexpr (MODE == 1) {   // the PG step's products with Z^T reach 2 (k_max + 1) columns
+      if (V == 9) {
+        if (bf) k_direct<MODE, 9, true, false><<<grid, 256, 0, st>>>(a);
+        else k_direct<MODE, 9, false, false><<<grid, 256, 0, st>>>(a);
+        return;
+      }
+    }
+    throw Error{BM_ERR_INVALID, "sparse pass: too many columns"};
 #undef BM_DIRECT_CASE
   }
   const size_t smem = pipe_smem_bytes(MODE, a.nchunk, bf);

@@ -4,6 +4,7 @@
 // control decisions (ranks, stopping, drops).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "dense.cuh"
@@ -24,7 +25,6 @@ struct ProxState {
   DenseWork dw;
   DevBuf<float> mbuf[17];   // m-side blocks
   DevBuf<float> Y, Bt;      // n-side blocks (ld ldq): L-application scratch, Z^T U^
-  DevBuf<float> YB;         // Z^T B_0 of the newest LmSVD block (ld ldq)
   DevBuf<float> YQ;         // Z^T Q of the Rayleigh-Ritz basis (ld ldq2)
   DevBuf<double> G, E, ev, S1, S2;
   DevBuf<float> Ts;
@@ -214,13 +214,14 @@ struct LmsvdOut {
 //
 // The subspace is the paper's: Q = [B_0, orth(B_1 | B_0)] with B_0 =
 // orth(L(U^)) the newest block and B_1 the previous one (memory p = 1).  The
-// Rayleigh-Ritz matrix Q^T L Q is formed as (Z^T Q)^T (Z^T Q) from images
-// Z^T B_0 (kept from the block's creation) and Z^T Q_2 of the new directions,
-// and L(U^) as Z (Z^T U^): in FP32 the product L = Z Z^T carries errors of
-// order eps * sigma_1^2 into every column, which would swamp the small
-// singular values near the threshold lambda * alpha, while products with Z
-// and Z^T alone err by eps * sigma_1 * (size of the column).  The small
-// eigenproblem runs in the relative-accuracy mode for the same reason.
+// Rayleigh-Ritz matrix Q^T L Q is formed as (Z^T Q)^T (Z^T Q) and L(U^) as
+// Z (Z^T U^): in FP32 the product L = Z Z^T carries errors of order
+// eps * sigma_1^2 into every column, which would swamp the small singular
+// values near the threshold lambda * alpha, while products with Z and Z^T
+// alone err by eps * sigma_1 * (size of the column).  The small eigenproblem
+// runs in the relative-accuracy mode for the same reason.  Each iteration
+// costs one product with Z^T (the basis Q) and one with Z (the Ritz vectors),
+// as one application of L would.
 LmsvdOut lmsvd_dev(bm_ctx& h, int c0, double alpha) {
   ProxState& ps = *h.ps;
   const bm_options& o = h.opt;
@@ -231,8 +232,6 @@ LmsvdOut lmsvd_dev(bm_ctx& h, int c0, double alpha) {
   const int k0 = orth_dev(h, mview(h, kUw, c0), nullptr, nullptr, nullptr, o.tau, -1, B[0], 0, -1);
   if (k0 == 0) return r;
   kc[0] = k0;
-  apply_zt(h, mview(h, B[0], k0), nview(h, ps.YB, k0), alpha);   // Z^T B_0
-  r.nL = 1;
   int nb = 1;
   const int k = k0;
   std::vector<double> theta_prev;
@@ -240,22 +239,16 @@ LmsvdOut lmsvd_dev(bm_ctx& h, int c0, double alpha) {
     r.iters = it;
     int q = kc[0];
     Tall Q = mview(h, B[0], kc[0]);
-    copy_cols_dev(h, nview(h, ps.YB, kc[0]), 0, Tall{ps.YQ.get(), n, kc[0], ps.ldq2}, 0, kc[0]);
     if (nb > 1) {
       copy_cols_dev(h, mview(h, B[0], kc[0]), 0, mview(h, kQ, kc[0]), 0, kc[0]);
       Tall F = mview(h, B[0], kc[0]);
-      const int c2 = orth_dev(h, mview(h, B[1], kc[1]), &F, nullptr, nullptr, o.tau, -1, kLQ, 0, -1);
-      if (c2 > 0) {
-        const Tall Q2 = mview(h, kLQ, c2);
-        apply_zt(h, Q2, nview(h, ps.Y, c2), alpha);                  // Z^T Q_2
-        r.nL += 1;
-        copy_cols_dev(h, Q2, 0, mview(h, kQ, kc[0] + c2), kc[0], c2);
-        copy_cols_dev(h, nview(h, ps.Y, c2), 0, Tall{ps.YQ.get(), n, kc[0] + c2, ps.ldq2}, kc[0], c2);
-      }
+      const int c2 = orth_dev(h, mview(h, B[1], kc[1]), &F, nullptr, nullptr, o.tau, -1, kQ, kc[0], -1);
       q = kc[0] + c2;
       Q = mview(h, kQ, q);
     }
     const Tall YQ{ps.YQ.get(), n, q, ps.ldq2};
+    apply_zt(h, Q, YQ, alpha);                                           // Z^T Q
+    r.nL += 1;
     gram_dev(h, ps.dw, YQ, YQ, ps.G.get(), false, "gram_rr");           // Q^T L Q
     sym_eig_dev(h, ps.dw, ps.G.get(), q, ps.ev.get(), ps.E.get(), kEigRelative);
     std::vector<double> th = to_host(h, ps.ev.get(), q);
@@ -282,8 +275,6 @@ LmsvdOut lmsvd_dev(bm_ctx& h, int c0, double alpha) {
     const int fb = B[2];
     const int cn = orth_dev(h, mview(h, kLB0, kk), nullptr, nullptr, nullptr, o.tau, -1, fb, 0, -1);
     if (cn == 0) break;
-    apply_zt(h, mview(h, fb, cn), nview(h, ps.YB, cn), alpha);         // Z^T B_new
-    r.nL += 1;
     // rotate: new block first, keep p older ones
     B[2] = B[1];
     B[1] = B[0];
@@ -416,7 +407,6 @@ void prox_create(bm_ctx& h) {
   ps.ldq2 = round_up4(2 * ps.qcap);
   for (auto& b : ps.mbuf) b.alloc((size_t)h.ix.m * ps.ldq2);
   ps.Y.alloc((size_t)h.ix.n * ps.ldq);
-  ps.YB.alloc((size_t)h.ix.n * ps.ldq);
   ps.YQ.alloc((size_t)h.ix.n * ps.ldq2);
 
   ps.Bt.alloc((size_t)h.ix.n * ps.ldq);
@@ -427,8 +417,8 @@ void prox_create(bm_ctx& h) {
   ps.S1.alloc(q2 * q2);
   ps.S2.alloc(q2 * q2);
   ps.Ts.alloc(q2 * ps.ldq2);
-  // q-wide SpMM partials need nslots x round_up4(qcap)
-  ensure_pass_scratch(h, ps.ldq);
+  // SpMM partials: slot rows as wide as the widest slice of a Z^T product
+  ensure_pass_scratch(h, std::min(ps.ldq2, kSpmmCols));
   ps.psi = h.opt.psi0;
 }
 
@@ -614,6 +604,87 @@ void tuning_spmm_dev(bm_ctx& h, bool csr) {
   const Tall nside = nview(h, ps.Y, q);
   if (csr) spmm_dev(h, true, h.r_csr.get(), nside, mside, -1.f);
   else spmm_dev(h, false, h.r_csc.get(), mside, nside, -1.f);
+}
+
+}  // namespace bm
+
+namespace bm {
+
+// Serialised PG-step state: the scalars of the warm start and safeguard
+// (Eq. "rt0", "rt0-1", "rt": ranks, psi_t, t) followed by U_t (m x ku),
+// U_{t-1} (m x ku2) and the truncated vector u (m, if present), FP32, rows
+// packed without padding.
+struct ProxSnap {
+  int32_t initialized, ku, ku2, have_u, rank_prev, rank_cur, prev_warm, t;
+  double psi;
+};
+
+size_t prox_state_bytes(const bm_ctx& h) {
+  const ProxState& ps = *h.ps;
+  const size_t m = (size_t)h.ix.m;
+  return sizeof(ProxSnap) + m * sizeof(float) * ((size_t)ps.ku + (size_t)std::max(ps.ku2, 0) + (ps.have_u ? 1 : 0));
+}
+
+namespace {
+void pack_cols(bm_ctx& h, uint8_t*& p, const float* src, int ld, int cols) {
+  if (cols <= 0 || h.ix.m == 0) return;
+  BM_CUDA(cudaMemcpy2DAsync(p, cols * sizeof(float), src, ld * sizeof(float), cols * sizeof(float), h.ix.m,
+                            cudaMemcpyDeviceToHost, h.stream));
+  p += (size_t)h.ix.m * cols * sizeof(float);
+}
+void unpack_cols(bm_ctx& h, const uint8_t*& p, float* dst, int ld, int cols) {
+  if (cols <= 0 || h.ix.m == 0) return;
+  BM_CUDA(cudaMemcpy2DAsync(dst, ld * sizeof(float), p, cols * sizeof(float), cols * sizeof(float), h.ix.m,
+                            cudaMemcpyHostToDevice, h.stream));
+  p += (size_t)h.ix.m * cols * sizeof(float);
+}
+}  // namespace
+
+void prox_state_save(bm_ctx& h, uint8_t* out) {
+  ProxState& ps = *h.ps;
+  ProxSnap s{ps.initialized ? 1 : 0, ps.ku, ps.ku2, ps.have_u ? 1 : 0, ps.rank_prev, ps.rank_cur, ps.prev_warm, ps.t,
+             ps.psi};
+  std::memcpy(out, &s, sizeof(s));
+  uint8_t* p = out + sizeof(s);
+  pack_cols(h, p, ps.mbuf[ps.iUprev].get(), ps.ldq2, ps.ku);
+  pack_cols(h, p, ps.mbuf[ps.iUprev2].get(), ps.ldq2, std::max(ps.ku2, 0));
+  if (ps.have_u) pack_cols(h, p, ps.mbuf[ps.iu].get(), 4, 1);
+  BM_CUDA(cudaStreamSynchronize(h.stream));
+}
+
+void prox_state_load(bm_ctx& h, const uint8_t* in, size_t len) {
+  ProxState& ps = *h.ps;
+  BM_REQUIRE(len >= sizeof(ProxSnap), BM_ERR_INVALID, "bm_set_state: truncated PG state");
+  ProxSnap s;
+  std::memcpy(&s, in, sizeof(s));
+  const int cap = 2 * ps.qcap;
+  BM_REQUIRE(s.ku >= 0 && s.ku <= cap && s.ku2 >= -1 && s.ku2 <= cap && s.prev_warm >= 0 && s.t >= 0 &&
+                 std::isfinite(s.psi),
+             BM_ERR_INVALID, "bm_set_state: invalid PG state");
+  const size_t m = (size_t)h.ix.m;
+  const size_t need =
+      sizeof(ProxSnap) + m * sizeof(float) * ((size_t)s.ku + (size_t)std::max(s.ku2, 0) + (s.have_u ? 1 : 0));
+  BM_REQUIRE(len == need, BM_ERR_INVALID, "bm_set_state: PG state size mismatch");
+  ps.initialized = s.initialized != 0;
+  ps.ku = s.ku;
+  ps.ku2 = s.ku2;
+  ps.have_u = s.have_u != 0;
+  ps.rank_prev = s.rank_prev;
+  ps.rank_cur = s.rank_cur;
+  ps.prev_warm = s.prev_warm;
+  ps.t = s.t;
+  ps.psi = s.psi;
+  ps.iUprev = kUprevA;
+  ps.iUprev2 = kUprevB;
+  ps.iu = kUvec;
+  const uint8_t* p = in + sizeof(ProxSnap);
+  unpack_cols(h, p, ps.mbuf[ps.iUprev].get(), ps.ldq2, ps.ku);
+  unpack_cols(h, p, ps.mbuf[ps.iUprev2].get(), ps.ldq2, std::max(ps.ku2, 0));
+  if (ps.have_u) {
+    BM_CUDA(cudaMemsetAsync(ps.mbuf[ps.iu].get(), 0, m * 4 * sizeof(float), h.stream));
+    unpack_cols(h, p, ps.mbuf[ps.iu].get(), 4, 1);
+  }
+  BM_CUDA(cudaStreamSynchronize(h.stream));
 }
 
 }  // namespace bm

@@ -74,12 +74,18 @@ size_t estimate_bytes(const Request& r, int prec) {
   size_t b = (size_t)nnz * (4 + 4 + 4 + 4 + 8 + 4 + 4 + 4);       // index, map, residual in both orders
   b += (size_t)nnz * 24;                                          // radix-sort scratch during create
   b += (size_t)(m + n) * ld * 4 * 8;                               // W, H, gradients, directions
-  b += (size_t)m * ld2 * 4 * 17 + (size_t)n * ld * 4 * 3 + (size_t)n * ld2 * 4;  // PG blocks
+  b += (size_t)m * ld2 * 4 * 17 + (size_t)n * ld * 4 * 2 + (size_t)n * ld2 * 4;  // PG blocks
   if (prec == 1) b += (size_t)(m + n) * ld * 2 * 3 + (size_t)std::max(m * ld2, n * ld) * 2;
   return b + b / 4 + (64u << 20);
 }
 
 void finish(bm_server_ctx& s, Active& a, bm_status st) {
+  if (st != BM_OK) {
+    // keep the failing request's message for bm_server_last_error
+    const std::string msg = "request " + std::to_string(a.req.id) + ": " + (a.h ? bm_last_error(a.h) : "create failed");
+    std::lock_guard<std::mutex> lk(s.mu);
+    s.err = msg;
+  }
   bm_request_result r{};
   r.id = a.req.id;
   r.status = st;

@@ -140,8 +140,8 @@ def test_init_step_parity(B, case):
 
 def test_solve_reaches_oracle_objective(B):
     """Algorithm 1 on the 500 x 300 planted problem (lambda = 0.5, k0 = 8): the
-    GPU reaches the oracle's converged objective within 1e-6 relative and the
-    same rank."""
+    GPU reaches the oracle's converged objective within 1e-6 relative, then
+    settles at the same rank and within 1e-8."""
     p = named_config("tiny")
     ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
     st, oinfo = O.solve(ix, p.lam, 8, 64, O.Options(), max_outer=300, tol=1e-13)
@@ -156,7 +156,15 @@ def test_solve_reaches_oracle_objective(B):
         Wi, Hi = _internal(ix, Wg, Hg)
         F_chk = O.objective(ix, Wi, Hi, p.lam)          # FP64 re-evaluation of the GPU iterate
         assert F_chk <= F_star * (1 + 2e-6)
-        assert r["k"] == st.W.shape[1]
+        # run on: the rank settles at the optimum's once the tail singular value
+        # has been thresholded away, and the FP32 path keeps the objective
+        # within 1e-8 of the FP64 optimum
+        r2 = B.bm_solve(h, max_outer=200, tol=0.0)
+        assert r2["k"] == st.W.shape[1]
+        assert abs(r2["F"] - F_star) <= 1e-8 * F_star
+        Wg, Hg = B.bm_get_factors(h, p.m, p.n)
+        Wi, Hi = _internal(ix, Wg, Hg)
+        assert abs(O.objective(ix, Wi, Hi, p.lam) - F_star) <= 1e-8 * F_star
     finally:
         B.bm_destroy(h)
 

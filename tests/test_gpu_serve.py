@@ -37,7 +37,9 @@ def _serve(B, probs, arrivals, **kw):
             ids.append(B.bm_server_submit(s, p.m, p.n, p.rows, p.cols, p.vals, p.lam, p.k_max))
         B.bm_server_drain(s, 600.0)
         res = {r["id"]: r for r in B.bm_server_results(s)}
-        return [res[i] for i in ids]
+        out = [res[i] for i in ids]
+        assert all(r["status"] == 0 for r in out), (out, B.binding.lib().bm_server_last_error(s))
+        return out
     finally:
         B.bm_server_destroy(s)
 
