@@ -507,6 +507,10 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
 // of V updated in parallel.  Sweeps stop when every off-diagonal entry is
 // below eps * sqrt(|a_pp a_qq|) or, for null blocks, eps * max|diag|.
 constexpr int kJacMax = 160;
+// FP32 relative rotation threshold of the refinement sweeps: a few units of
+// FP32 rounding above it, so that the sweeps terminate (a threshold at the
+// rounding level itself keeps rotating on rounding noise).
+constexpr float kJacRelTol = 2e-6f;
 constexpr int kJacThreads = 512;
 
 __device__ __forceinline__ void rr_pair(int r, int k, int np, int& p, int& q) {
@@ -522,7 +526,7 @@ __device__ __forceinline__ void rr_pair(int r, int k, int np, int& p, int& q) {
 
 template <typename T>
 __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __restrict__ S, int n, int max_sweeps,
-                                                          double* __restrict__ evals, double* __restrict__ evecs,
+                                                          T tol, double* __restrict__ evals, double* __restrict__ evecs,
                                                           int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char jac_raw[];
   T* jac_sm = reinterpret_cast<T*>(jac_raw);
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __rest
   __shared__ int pp_[kJacMax / 2], qq_[kJacMax / 2];
   __shared__ int sh_rot;
   __shared__ T sh_floor;
-  const T eps = sizeof(T) == 8 ? (T)4e-15 : (T)1e-7;
+  const T eps = tol;   // rotate while |a_pq| > tol * sqrt(|a_pp a_qq|)
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int idx = tid; idx < np * np; idx += nt) {
     const int i = idx / np, j = idx - i * np;
@@ -888,12 +892,12 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
       const size_t smem = (size_t)2 * npd * npd * sizeof(double);
       BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       BM_LAUNCH(h, "jacobi_eig_f64",
-                k_jacobi_eig<double><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, evals, T1, w.status.get()));
+                k_jacobi_eig<double><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, 4e-15, evals, T1, w.status.get()));
     } else {
       const size_t smem = (size_t)2 * npd * npd * sizeof(float);
       BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       BM_LAUNCH(h, "jacobi_eig_rel",
-                k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, evals, T1, w.status.get()));
+                k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, kJacRelTol, evals, T1, w.status.get()));
     }
     BM_LAUNCH(h, "eig_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(V, T1, evecs, n, n, n, 0));
     int st = 0;
@@ -911,7 +915,7 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
     BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
     BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     BM_LAUNCH(h, "jacobi_eig_f32",
-              k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S, n, 30, evals, evecs, w.status.get()));
+              k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S, n, 30, 1e-7f, evals, evecs, w.status.get()));
     int st = 0;
     BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
     BM_CUDA(cudaStreamSynchronize(h.stream));

@@ -414,19 +414,23 @@ __device__ __forceinline__ float4 gather4(const float* g, const void* gb, int64_
   return __ldg(reinterpret_cast<const float4*>(g + j * ld) + c);
 }
 
+// Lanes that share one entry (its row split into float4 chunks l, l + L, ...).
+constexpr int kLanesPerEntry = 4;
+
 // One segment s of a pass (the warp's lanes cooperate).  EX: the row width is
 // exactly 4 V chunks of 4 floats, so no chunk needs a bounds test.
 template <int MODE, int V, bool BF, bool EX>
 __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
   constexpr unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
+  constexpr int EPS = 32 / kLanesPerEntry;   // entries per step
+  const int lane = threadIdx.x & 31, g = lane / kLanesPerEntry, l = lane % kLanesPerEntry;
   const int nch = a.nchunk;
   const int i = a.seg_row[s];
   const int64_t beg = a.seg_beg[s], end = a.seg_end[s];
   float4 w[V], dw[V], acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const int c = l + 4 * v;
+    const int c = l + kLanesPerEntry * v;
     const bool in = (EX || c < nch);
     w[v] = (MODE != 1 && in) ? __ldg(reinterpret_cast<const float4*>(a.o0 + (int64_t)i * a.ld) + c)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -441,8 +445,8 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
     const int j = valid ? __ldg(a.idx + e) : 0;
     const float sv = valid ? __ldg(a.scal + e) : 0.f;
 #pragma unroll 2
-    for (int t = 0; t < 4; ++t) {
-      const int src = t * 8 + g;
+    for (int t = 0; t < kLanesPerEntry; ++t) {
+      const int src = t * EPS + g;
       const int64_t jj = __shfl_sync(FULL, j, src);
       const float sc = __shfl_sync(FULL, sv, src);
       const bool ok = e0 + src < end;
@@ -451,12 +455,12 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
         float d = 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          const int c = l + 4 * v;
+          const int c = l + kLanesPerEntry * v;
           hv[v] = (EX || c < nch) ? gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c) : make_float4(0.f, 0.f, 0.f, 0.f);
           d = fmaf(w[v].x, hv[v].x, fmaf(w[v].y, hv[v].y, fmaf(w[v].z, hv[v].z, fmaf(w[v].w, hv[v].w, d))));
         }
-        d += __shfl_xor_sync(FULL, d, 1);
-        d += __shfl_xor_sync(FULL, d, 2);
+#pragma unroll
+        for (int mk = 1; mk < kLanesPerEntry; mk <<= 1) d += __shfl_xor_sync(FULL, d, mk);
         const float r = ok ? d - sc : 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -473,7 +477,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
         const float vv = ok ? sc : 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          const int c = l + 4 * v;
+          const int c = l + kLanesPerEntry * v;
           if ((EX || c < nch)) {
             const float4 x = gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c);
             acc[v].x = fmaf(vv, x.x, acc[v].x);
@@ -486,7 +490,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
         float b = 0.f, c2 = 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          const int c = l + 4 * v;
+          const int c = l + kLanesPerEntry * v;
           if ((EX || c < nch)) {
             const float4 h = gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c);
             const float4 dh = gather4<BF>(a.g1, a.g1b, jj, a.ld, a.ldb, c);
@@ -495,10 +499,11 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
             c2 = fmaf(dw[v].x, dh.x, fmaf(dw[v].y, dh.y, fmaf(dw[v].z, dh.z, fmaf(dw[v].w, dh.w, c2))));
           }
         }
-        b += __shfl_xor_sync(FULL, b, 1);
-        b += __shfl_xor_sync(FULL, b, 2);
-        c2 += __shfl_xor_sync(FULL, c2, 1);
-        c2 += __shfl_xor_sync(FULL, c2, 2);
+#pragma unroll
+        for (int mk = 1; mk < kLanesPerEntry; mk <<= 1) {
+          b += __shfl_xor_sync(FULL, b, mk);
+          c2 += __shfl_xor_sync(FULL, c2, mk);
+        }
         if (ok && l == 0) {
           s_rb = fmaf(sc, b, s_rb);
           s_bb = fmaf(b, b, fmaf(2.f * sc, c2, s_bb));
@@ -512,7 +517,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
 #pragma unroll
-      for (int mk = 4; mk < 32; mk <<= 1) {
+      for (int mk = kLanesPerEntry; mk < 32; mk <<= 1) {
         acc[v].x += __shfl_xor_sync(FULL, acc[v].x, mk);
         acc[v].y += __shfl_xor_sync(FULL, acc[v].y, mk);
         acc[v].z += __shfl_xor_sync(FULL, acc[v].z, mk);
@@ -523,7 +528,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
       const int slot = a.seg_slot[s];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        const int c = l + 4 * v;
+        const int c = l + kLanesPerEntry * v;
         if ((EX || c < nch)) {
           if (slot < 0) {
             float4* op = reinterpret_cast<float4*>(a.out + (int64_t)i * a.ld_out + 4 * c);
@@ -600,10 +605,10 @@ __global__ void __launch_bounds__(256, 3) k_direct_batch(const PipeArgs* __restr
 template <int MODE>
 void launch_direct_batch(const PipeArgs* args_d, const int64_t* prefix_d, int count, int64_t total_segs,
                          int nchunk, bool bf, cudaStream_t st) {
-  const int V = (nchunk + 3) / 4;
+  const int V = (nchunk + kLanesPerEntry - 1) / kLanesPerEntry;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(total_segs, 1), 8),
                                                                (int64_t)num_sms() * 24));
-  const bool ex = nchunk == 4 * V;
+  const bool ex = nchunk == kLanesPerEntry * V;
 #define BM_DBATCH_CASE(VV)                                                                          \
   case VV:                                                                                          \
     if (bf) {                                                                                       \
@@ -643,11 +648,11 @@ inline bool use_pipe_kernel() {
 // BF16 copies (a.g0b, a.g1b) for the gathered rows.
 template <int MODE>
 void launch_pipe(const PipeArgs& a, cudaStream_t st, bool bf = false) {
-  const int V = (a.nchunk + 3) / 4;
   if (!use_pipe_kernel()) {
+    const int V = (a.nchunk + kLanesPerEntry - 1) / kLanesPerEntry;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(a.nseg, 1), 8),
                                                                  (int64_t)num_sms() * 24));
-    const bool ex = a.nchunk == 4 * V;
+    const bool ex = a.nchunk == kLanesPerEntry * V;
 #define BM_DIRECT_CASE(VV)                                                  \
   case VV:                                                                  \
     if (bf) {                                                               \
@@ -680,6 +685,7 @@ void launch_pipe(const PipeArgs& a, cudaStream_t st, bool bf = false) {
     throw Error{BM_ERR_INVALID, "sparse pass: too many columns"};
 #undef BM_DIRECT_CASE
   }
+  const int V = (a.nchunk + 3) / 4;
   const size_t smem = pipe_smem_bytes(MODE, a.nchunk, bf);
   const int warps = kPipeWarps;
   const int blocks_per_sm = (int)std::max<size_t>(1, (200 * 1024) / std::max<size_t>(smem, 1));
