@@ -169,7 +169,9 @@ def run_ours(args):
     t_gen = time.time()
     p = named_config(args.config)
     t_gen = time.time() - t_gen
-    h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, p.k_max)
+    opt = B.bm_default_options()
+    opt.precision = args.precision
+    h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, p.k_max, opt)
     stream = torch.cuda.Stream()
     B.bm_set_stream(h, stream)
     d = B.bm_dims(h)
@@ -287,7 +289,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f32" if args.precision == 0 else "bf16 gathers, f32 accumulation",
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}-shaped 480189x17770, nnz=100480507, Zipf(1.2), ratings 1..5",
                    "lambda": p.lam, "k": k, "k_end": k_now, "step": "3 BM iterations + 1 inexact PG step"
@@ -522,6 +524,73 @@ def run_serve(args):
     }
 
 
+def run_edm(args):
+    """Distance-geometry loss/gradient (Eq. EDM) on the 30,000-point chain,
+    k = 16: one step = one bm_edm_loss_grad; value = pairs / s."""
+    import torch
+
+    import paper_2204_14067_gb300 as B
+    from synth import self_avoiding_chain
+
+    p = self_avoiding_chain(n=30_000, seed=3)
+    k = 16
+    lam = -10.0 * np.sqrt(p.n) / float(np.sum(p.d.astype(np.float64) ** 2))   # lambda of the conformation workload
+    rng = np.random.default_rng(5)
+    V = (p.X_true @ rng.standard_normal((3, k)) * 0.3 + 0.05 * rng.standard_normal((p.n, k))).astype(np.float32)
+    h = B.bm_edm_create(p.n, p.i, p.j, p.d, lam, k)
+    stream = torch.cuda.Stream()
+    B.bm_edm_set_stream(h, stream)
+    B.bm_edm_set_factor(h, k, V)
+    gV = torch.empty((p.n, k), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        B.bm_edm_loss_grad(h, gV)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        B.bm_edm_loss_grad(h, gV)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        B.bm_edm_set_factor(h, k, V)
+        gh = np.empty_like(V)
+        B.bm_edm_loss_grad(h, gh)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    B.bm_edm_destroy(h)
+    pairs = p.npairs
+    by = 2 * pairs * 8 + 2 * p.n * k * 4        # both directions: column + d^2 per stored pair; V in, gradient out
+    fl = 2 * pairs * 6 * k                      # residual (3k) and gradient update (3k) per stored pair
+    peaks, kind = _load_peaks()
+    ach = by / (ms / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu:
+        from oracle import bm_oracle as O
+        V64 = V.astype(np.float64)
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0 and reps < 20:
+            O.edm_loss_grad(V64, p.i, p.j, p.d, 1.0, lam)
+            reps += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": pairs * reps / el, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"the full problem, {reps} evaluations, {el:.1f} s"}
+    return {
+        "metric": "EDM gradient pairs/s", "value": pairs / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"3-D self-avoiding chain, n = {p.n}, {pairs} pairs within 6.0, k = {k}",
+                   "l2": "problem fits in L2 (about 30 MB): cached between steps"},
+        "e2e": {"value": pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(V.nbytes),
+                "d2h_bytes_per_step": int(V.nbytes)},
+        "roofline": {"bound": "hbm", "kernel": "edm", "achieved": ach, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                     "frac": ach / float(peaks["hbm_gbs"]), "traffic": None, "peak_source": kind,
+                     "bytes_per_launch": by, "flops_per_launch": fl},
+        "cpu_baseline": cpu,
+    }
+
+
 def _dist_cpu():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return None, int(os.environ.get("RANK", "0")), ws
@@ -533,7 +602,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="cycle", choices=["cycle", "grad", "tto", "serve"])
+    ap.add_argument("--mode", default="cycle", choices=["cycle", "grad", "tto", "serve", "edm"])
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="1: BF16 copies of the gathered factor rows (cycle and grad modes)")
     ap.add_argument("--serve-count", type=int, default=24)
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true")
@@ -547,6 +618,8 @@ def main():
         line = run_tto(args)
     elif args.mode == "serve":
         line = run_serve(args)
+    elif args.mode == "edm":
+        line = run_edm(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -347,6 +347,9 @@ bm_status bm_edm_set_factor(bm_edm_handle h, int32_t k, const float* V);
 /* *g (host, nullable) = g(V); gV float[n*k] (host or device, nullable) = grad g(V).
  * Errors: BM_ERR_NUMERIC if g is not finite. */
 bm_status bm_edm_loss_grad(bm_edm_handle h, double* g, float* gV);
+/* Run the handle's calls on `stream` (a cudaStream_t; NULL: the handle's own
+ * stream).  Work queued on the previous stream is finished first. */
+bm_status bm_edm_set_stream(bm_edm_handle h, void* stream);
 
 /*
  * bm_loss_grad_csr_noalloc -- the loss and W-side gradient of (MF) for

@@ -303,6 +303,7 @@ _SIGS.update({
     "bm_edm_last_error": (_c.c_char_p, [_P]),
     "bm_edm_set_factor": (_c.c_int, [_P, _c.c_int32, _P]),
     "bm_edm_loss_grad": (_c.c_int, [_P, _P, _P]),
+    "bm_edm_set_stream": (_c.c_int, [_P, _P]),
 })
 
 
@@ -325,6 +326,11 @@ def bm_edm_destroy(h):
 
 def bm_edm_set_factor(h, k, V):
     _check_edm(lib().bm_edm_set_factor(h, int(k), _ptr(V)), h)
+
+
+def bm_edm_set_stream(h, stream):
+    ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    _check_edm(lib().bm_edm_set_stream(h, ctypes.c_void_p(ptr)), h)
 
 
 def bm_edm_loss_grad(h, gV=None):

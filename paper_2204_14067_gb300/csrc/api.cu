@@ -4,7 +4,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
 
 #include "ctx.cuh"
 
@@ -19,6 +21,23 @@ int num_sms() {
     if (cached <= 0) cached = 1;
   }
   return cached;
+}
+
+void allow_max_smem(const void* kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  BM_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, kernel})) return;
+  int optin = 0;
+  BM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  BM_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  // static and dynamic shared memory together may not exceed the opt-in limit
+  BM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes));
+  done.insert({dev, kernel});
 }
 
 bool is_device_ptr(const void* ptr) {

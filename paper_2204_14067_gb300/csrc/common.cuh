@@ -19,10 +19,13 @@ struct Error {
   std::string msg;
 };
 
+// A failed call throws; the runtime's last-error state is cleared first so
+// that a later launch check does not report this failure again.
 #define BM_CUDA(call)                                                                   \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \
     if (e_ != cudaSuccess) {                                                            \
+      (void)cudaGetLastError();                                                         \
       throw ::bm::Error{e_ == cudaErrorMemoryAllocation ? BM_ERR_OOM : BM_ERR_CUDA,     \
                         std::string(#call) + ": " + cudaGetErrorString(e_)};            \
     }                                                                                   \
@@ -67,5 +70,12 @@ int num_sms();
 
 // True if ptr is a device (or managed) address.
 bool is_device_ptr(const void* ptr);
+
+// Raise `kernel`'s dynamic shared-memory limit to the device's opt-in
+// maximum, once per process and device.  The limit is a per-function
+// attribute shared by all host threads: setting it to each launch's own size
+// right before the launch races with other threads' launches of the same
+// kernel (a smaller value set in between makes their launch fail).
+void allow_max_smem(const void* kernel);
 
 }  // namespace bm

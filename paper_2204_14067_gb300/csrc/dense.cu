@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
     const T v0 = x0 - alpha;
     const T vtv = ss - x0 * x0 + v0 * v0;
     const T beta = vtv > 0 ? (T)2 / vtv : (T)0;
+    __syncthreads();   // every thread has read x0 before thread 0 overwrites it
     if (tid < L) {
       const T v = tid == 0 ? v0 : x;
       vv[tid] = v;
@@ -468,6 +469,9 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
       }
       __syncthreads();
       const int m = sh_m, cnt = sh_cnt;
+      // every thread has read sh_m before warp 0 may overwrite it (after a
+      // break it goes straight on to the next search)
+      __syncthreads();
       if (m == l) break;
       for (int q = tid; q < n; q += nt) {
         T zf = Z[m * n + q];
@@ -603,7 +607,10 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __rest
       }
       __syncthreads();
     }
-    if (!sh_rot) break;
+    // read the flag everywhere before thread 0 resets it for the next sweep
+    const int rot = sh_rot;
+    __syncthreads();
+    if (!rot) break;
   }
   // sort the first n diagonal entries descending (the padding index stays out)
   for (int i = tid; i < n; i += nt) {
@@ -636,7 +643,7 @@ __global__ void k_small_mm_tn(const double* __restrict__ A, const double* __rest
 // definite (the Gram of an almost orthonormal block).  One block, FP32,
 // right-looking factorisation then one column of the inverse per thread.
 __global__ void __launch_bounds__(512) k_chol_inv(const double* __restrict__ S, int n, float* __restrict__ T, int ldt,
-                                                int* __restrict__ status) {
+                                                int* __restrict__ status, double* __restrict__ inv_fro2) {
   extern __shared__ __align__(16) float ch_sm[];
   float* A = ch_sm;  // n x n, upper triangle holds R
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -663,12 +670,28 @@ __global__ void __launch_bounds__(512) k_chol_inv(const double* __restrict__ S, 
     }
     __syncthreads();
   }
-  // X = R^{-1}: column c solves R x = e_c by back substitution (thread per column)
+  // X = R^{-1}: column c solves R x = e_c by back substitution (thread per
+  // column); ||R^{-1}||_F^2 is summed on the way
+  double sq = 0.0;
   for (int c = tid; c < n; c += nt) {
     for (int i = n - 1; i >= 0; --i) {
       float acc = (i == c) ? 1.f : 0.f;
       for (int k = i + 1; k <= c; ++k) acc -= A[i * n + k] * T[k * ldt + c];
-      T[i * ldt + c] = i > c ? 0.f : acc / A[i * n + i];
+      const float x = i > c ? 0.f : acc / A[i * n + i];
+      T[i * ldt + c] = x;
+      sq += (double)x * (double)x;
+    }
+  }
+  if (inv_fro2) {
+    __shared__ double red[16];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
+    if ((tid & 31) == 0) red[tid >> 5] = sq;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (nt >> 5); ++w) t += red[w];
+      *inv_fro2 = t;
     }
   }
   __syncthreads();
@@ -802,10 +825,10 @@ void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, 
   float2* part = reinterpret_cast<float2*>(w.gram_part.get());
   dim3 grid((unsigned)gx, (unsigned)gy);
   if (compensated) {
-    BM_CUDA(cudaFuncSetAttribute(k_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    allow_max_smem((const void*)k_gram<true>);
     BM_LAUNCH(h, tag, k_gram<true><<<grid, threads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab, sym, part));
   } else {
-    BM_CUDA(cudaFuncSetAttribute(k_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    allow_max_smem((const void*)k_gram<false>);
     BM_LAUNCH(h, tag, k_gram<false><<<grid, threads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab, sym, part));
   }
   BM_LAUNCH(h, "gram_reduce", k_gram_reduce<<<(unsigned)ceil_div((int64_t)a * b, 32), 256, 0, h.stream>>>(
@@ -826,7 +849,7 @@ void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, 
   const int R = 8 * groups;
   const size_t smem = (size_t)a * nb4 * sizeof(float4) + (size_t)4 * a4 * R * sizeof(float);
   BM_REQUIRE(smem <= 200 * 1024, BM_ERR_INVALID, "gemm: block too large");
-  BM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  allow_max_smem((const void*)k_gemm);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A.rows, R), (int64_t)num_sms() * 3));
   BM_LAUNCH(h, tag, k_gemm<<<grid, kGemmThreads, smem, h.stream>>>(A.p, A.ld, a, C, ldc, b, Y.p, Y.ld, A.rows,
                                                                    beta, gamma, groups));
@@ -890,12 +913,12 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
     BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
     if (jac64) {
       const size_t smem = (size_t)2 * npd * npd * sizeof(double);
-      BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      allow_max_smem((const void*)k_jacobi_eig<double>);
       BM_LAUNCH(h, "jacobi_eig_f64",
                 k_jacobi_eig<double><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, 4e-15, evals, T1, w.status.get()));
     } else {
       const size_t smem = (size_t)2 * npd * npd * sizeof(float);
-      BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      allow_max_smem((const void*)k_jacobi_eig<float>);
       BM_LAUNCH(h, "jacobi_eig_rel",
                 k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, kJacRelTol, evals, T1, w.status.get()));
     }
@@ -913,7 +936,7 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
     const size_t smem = (size_t)2 * np * np * sizeof(float);
     w.status.alloc(1);
     BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
-    BM_CUDA(cudaFuncSetAttribute(k_jacobi_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_smem((const void*)k_jacobi_eig<float>);
     BM_LAUNCH(h, "jacobi_eig_f32",
               k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S, n, 30, 1e-7f, evals, evecs, w.status.get()));
     int st = 0;
@@ -934,13 +957,13 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
   if (!(a_sm && z_sm)) gbuf.alloc(2 * (size_t)kEigMax * kEigMax);
   const size_t smem = (a_sm + z_sm) * nn;
   if (dbl) {
-    BM_CUDA(cudaFuncSetAttribute(k_sym_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+    allow_max_smem((const void*)k_sym_eig<double>);
     double* gA = gbuf.get();
     double* gZ = gbuf.get() ? gbuf.get() + (size_t)kEigMax * kEigMax : nullptr;
     BM_LAUNCH(h, "sym_eig_f64", k_sym_eig<double><<<1, kEigThreads, smem, h.stream>>>(
                                     S, n, evals, evecs, gA, gZ, a_sm, z_sm, w.status.get()));
   } else {
-    BM_CUDA(cudaFuncSetAttribute(k_sym_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+    allow_max_smem((const void*)k_sym_eig<float>);
     float* gA = reinterpret_cast<float*>(gbuf.get());
     float* gZ = gA ? gA + (size_t)kEigMax * kEigMax : nullptr;
     BM_LAUNCH(h, "sym_eig_f32", k_sym_eig<float><<<1, kEigThreads, smem, h.stream>>>(
@@ -952,17 +975,36 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
   BM_REQUIRE(st == 0, BM_ERR_NUMERIC, st & 2 ? "eigensolver: non-finite eigenvalue" : "eigensolver: QL did not converge");
 }
 
-void chol_inv_dev(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt) {
+namespace {
+// Returns the status word (0: R^{-1} in T) and, with fro2, ||R^{-1}||_F^2.
+int chol_inv_run(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt, double* fro2) {
   BM_REQUIRE(n >= 1 && n <= 200, BM_ERR_INVALID, "cholesky: size out of range");
   const size_t smem = (size_t)n * n * sizeof(float);
   w.status.alloc(1);
+  w.scratch.alloc(1);
   BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
-  BM_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  BM_LAUNCH(h, "chol_inv", k_chol_inv<<<1, 512, smem, h.stream>>>(S, n, T, ldt, w.status.get()));
+  allow_max_smem((const void*)k_chol_inv);
+  BM_LAUNCH(h, "chol_inv", k_chol_inv<<<1, 512, smem, h.stream>>>(S, n, T, ldt, w.status.get(),
+                                                                  fro2 ? w.scratch.get() : nullptr));
   int st = 0;
   BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+  if (fro2) BM_CUDA(cudaMemcpyAsync(fro2, w.scratch.get(), sizeof(double), cudaMemcpyDeviceToHost, h.stream));
   BM_CUDA(cudaStreamSynchronize(h.stream));
+  return st;
+}
+}  // namespace
+
+void chol_inv_dev(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt) {
+  const int st = chol_inv_run(h, w, S, n, T, ldt, nullptr);
   BM_REQUIRE(st == 0, BM_ERR_NUMERIC, "cholesky: Gram matrix not positive definite");
+}
+
+bool chol_inv_try_dev(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt, double* inv_fro2) {
+  double f = 0.0;
+  const int st = chol_inv_run(h, w, S, n, T, ldt, &f);
+  if (st != 0 || !std::isfinite(f)) return false;
+  *inv_fro2 = f;
+  return true;
 }
 
 void select_scale_dev(bm_ctx& h, const double* E, int n, int rows, const int* cols_h, const double* scale_h,

@@ -57,6 +57,9 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
 // T (n x n FP32, ld ldt) = R^{-1}, R^T R = S (S FP64 n x n, positive definite).
 // Throws BM_ERR_NUMERIC if a pivot is not positive.
 void chol_inv_dev(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt);
+// As chol_inv_dev, returning false instead of throwing when a pivot is not
+// positive; on success *inv_fro2 = ||R^{-1}||_F^2, so lambda_min(S) >= 1 / *inv_fro2.
+bool chol_inv_try_dev(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt, double* inv_fro2);
 
 // T (rows x cols FP32, ld) = E(0:rows, cols_idx) * diag(scale)  (E FP64 n x n)
 void select_scale_dev(bm_ctx& h, const double* E, int n, int rows, const int* cols_h, const double* scale_h,

@@ -13,7 +13,8 @@ struct bm_edm_ctx {
   int64_t n = 0, npairs = 0;
   double lambda = 0;
   int k_max = 0, k = 0, ld = 4;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;      // stream the calls run on
+  cudaStream_t own_stream = nullptr;  // the handle's own stream
   bm::DevBuf<int64_t> row_ptr;
   bm::DevBuf<int32_t> col;
   bm::DevBuf<float> dsq, w;    // d_ij^2 and w_ij in CSR order
@@ -257,7 +258,8 @@ bm_status bm_edm_create(int64_t n, int64_t npairs, const int32_t* i, const int32
     h->npairs = npairs;
     h->lambda = lambda;
     h->k_max = k_max;
-    BM_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    BM_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
     cudaStream_t s = h->stream;
     DevBuf<int32_t> ti, tj;
     DevBuf<float> td, tw;
@@ -323,9 +325,19 @@ bm_status bm_edm_create(int64_t n, int64_t npairs, const int32_t* i, const int32
 void bm_edm_destroy(bm_edm_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  cudaStream_t s = h->stream;
+  cudaStream_t s = h->own_stream;
   delete h;
   if (s) cudaStreamDestroy(s);
+}
+
+bm_status bm_edm_set_stream(bm_edm_handle h, void* stream) {
+  if (!h) return BM_ERR_INVALID;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    h->err = "bm_edm_set_stream: synchronising the previous stream failed";
+    return BM_ERR_CUDA;
+  }
+  h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+  return BM_OK;
 }
 
 const char* bm_edm_last_error(bm_edm_handle h) { return h ? h->err.c_str() : g_edm_error.c_str(); }

@@ -414,14 +414,22 @@ __device__ __forceinline__ float4 gather4(const float* g, const void* gb, int64_
   return __ldg(reinterpret_cast<const float4*>(g + j * ld) + c);
 }
 
-// Lanes that share one entry (its row split into float4 chunks l, l + L, ...).
-constexpr int kLanesPerEntry = 4;
+// Lanes that share one entry (its row split into float4 chunks l, l + L, ...)
+// and resident blocks per SM, by pass mode: the line-search pass (two
+// gathered rows, three dot products) runs fastest with eight lanes per entry
+// and four blocks per SM, the single-gather passes with four lanes and three
+// blocks (measured on the recommendation-scale workload at k = 64).
+template <int MODE>
+constexpr int lanes_per_entry() { return MODE == 2 ? 8 : 4; }
+template <int MODE>
+constexpr int direct_blocks_per_sm() { return MODE == 2 ? 4 : 3; }
 
 // One segment s of a pass (the warp's lanes cooperate).  EX: the row width is
 // exactly 4 V chunks of 4 floats, so no chunk needs a bounds test.
 template <int MODE, int V, bool BF, bool EX>
 __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int kLanesPerEntry = lanes_per_entry<MODE>();
   constexpr int EPS = 32 / kLanesPerEntry;   // entries per step
   const int lane = threadIdx.x & 31, g = lane / kLanesPerEntry, l = lane % kLanesPerEntry;
   const int nch = a.nchunk;
@@ -576,7 +584,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
 }
 
 template <int MODE, int V, bool BF, bool EX>
-__global__ void __launch_bounds__(256, 3) k_direct(PipeArgs a) {
+__global__ void __launch_bounds__(256, direct_blocks_per_sm<MODE>()) k_direct(PipeArgs a) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < a.nseg; s += nwarps)
     direct_segment<MODE, V, BF, EX>(a, s);
@@ -586,7 +594,7 @@ __global__ void __launch_bounds__(256, 3) k_direct(PipeArgs a) {
 // concatenated segment lists belongs to problem p with
 // prefix[p] <= sg < prefix[p + 1].
 template <int MODE, int V, bool BF, bool EX>
-__global__ void __launch_bounds__(256, 3) k_direct_batch(const PipeArgs* __restrict__ args,
+__global__ void __launch_bounds__(256, direct_blocks_per_sm<MODE>()) k_direct_batch(const PipeArgs* __restrict__ args,
                                                          const int64_t* __restrict__ prefix, int count) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = prefix[count];
@@ -605,6 +613,7 @@ __global__ void __launch_bounds__(256, 3) k_direct_batch(const PipeArgs* __restr
 template <int MODE>
 void launch_direct_batch(const PipeArgs* args_d, const int64_t* prefix_d, int count, int64_t total_segs,
                          int nchunk, bool bf, cudaStream_t st) {
+  constexpr int kLanesPerEntry = lanes_per_entry<MODE>();
   const int V = (nchunk + kLanesPerEntry - 1) / kLanesPerEntry;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(total_segs, 1), 8),
                                                                (int64_t)num_sms() * 24));
@@ -649,6 +658,7 @@ inline bool use_pipe_kernel() {
 template <int MODE>
 void launch_pipe(const PipeArgs& a, cudaStream_t st, bool bf = false) {
   if (!use_pipe_kernel()) {
+    constexpr int kLanesPerEntry = lanes_per_entry<MODE>();
     const int V = (a.nchunk + kLanesPerEntry - 1) / kLanesPerEntry;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(a.nseg, 1), 8),
                                                                  (int64_t)num_sms() * 24));
@@ -694,12 +704,10 @@ void launch_pipe(const PipeArgs& a, cudaStream_t st, bool bf = false) {
 #define BM_PIPE_CASE(VV)                                                                               \
   case VV: {                                                                                           \
     if (bf) {                                                                                          \
-      BM_CUDA(cudaFuncSetAttribute(k_pipe<MODE, VV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                   (int)smem));                                                        \
+      allow_max_smem((const void*)k_pipe<MODE, VV, true>);                                                        \
       k_pipe<MODE, VV, true><<<grid, warps * 32, smem, st>>>(a);                                       \
     } else {                                                                                           \
-      BM_CUDA(cudaFuncSetAttribute(k_pipe<MODE, VV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                   (int)smem));                                                        \
+      allow_max_smem((const void*)k_pipe<MODE, VV, false>);                                                        \
       k_pipe<MODE, VV, false><<<grid, warps * 32, smem, st>>>(a);                                      \
     }                                                                                                  \
     break;                                                                                             \

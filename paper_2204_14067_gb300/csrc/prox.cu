@@ -41,6 +41,9 @@ struct ProxState {
 
 namespace {
 
+// Smallest Gram eigenvalue bound for which orth() takes the Cholesky basis.
+constexpr double kOrthCholCert = 1e-2;
+
 enum { kUprevA = 0, kUprevB = 1, kUvec = 2, kU = 3, kB0 = 4, kLB0 = 5, kB1 = 6, kLB1 = 7, kB2 = 8, kLB2 = 9,
        kQ = 10, kLQ = 11, kX1 = 12, kX2 = 13, kX3 = 14, kX4 = 15, kUw = 16 };
 
@@ -148,7 +151,20 @@ int orth_dev(bm_ctx& h, const Tall& M, const Tall* F, const Tall* LM, const Tall
     }
     gram_dev(h, ps.dw, Mh, Mh, ps.G.get(), true, "gram_orth");
     int c2 = c1;
-    if (pass == 0) {
+    bool chol_basis = false;
+    if (pass == 0 && (max_cols < 0 || max_cols >= c1)) {
+      // Eq. "orth-W" keeps every direction when no Gram eigenvalue is <= tau.
+      // A Cholesky factor P^T P = R^T R certifies that: lambda_min >= 1 /
+      // ||R^{-1}||_F^2.  Then P R^{-1} is an orthonormal basis of the same
+      // span, found without the eigensolver (the certificate also bounds the
+      // condition number so that the FP32 second pass restores orthogonality).
+      double f = 0.0;
+      chol_basis = chol_inv_try_dev(h, ps.dw, ps.G.get(), c1, ps.Ts.get(), ps.ldq2, &f) && f > 0 &&
+                   1.0 / f >= std::max(kOrthCholCert, 10.0 * tau);
+    }
+    if (chol_basis) {
+      // Ts = R^{-1}, all c1 columns kept
+    } else if (pass == 0) {
       // Eq. "orth-W": eigen-decomposition of P^T P, drop eigenvalues <= tau, scale by Lambda^{-1/2}
       sym_eig_dev(h, ps.dw, ps.G.get(), c1, ps.ev.get(), ps.E.get(), kEigFast);
       std::vector<double> lam = to_host(h, ps.ev.get(), c1);

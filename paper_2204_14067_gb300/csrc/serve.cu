@@ -82,7 +82,7 @@ size_t estimate_bytes(const Request& r, int prec) {
 void finish(bm_server_ctx& s, Active& a, bm_status st) {
   if (st != BM_OK) {
     // keep the failing request's message for bm_server_last_error
-    const std::string msg = "request " + std::to_string(a.req.id) + ": " + (a.h ? bm_last_error(a.h) : "create failed");
+    const std::string msg = "request " + std::to_string(a.req.id) + ": " + bm_last_error(a.h);
     std::lock_guard<std::mutex> lk(s.mu);
     s.err = msg;
   }
@@ -179,20 +179,27 @@ void run_batched(bm_server_ctx& s) {
       s.cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return s.stop.load() || !s.queue.empty(); });
       continue;
     }
-    // BM phase of every active solve as one batch
+    // BM phase of every active solve of rank >= 1 as one batch (a rank-0
+    // iterate has no factors to move; its next PG step starts from X = 0)
     std::vector<bm_handle> set;
-    for (auto& a : act) set.push_back(a.h);
+    std::vector<size_t> in_batch;
+    for (size_t i = 0; i < act.size(); ++i) {
+      int32_t k = 0;
+      bm_dims(act[i].h, nullptr, nullptr, nullptr, nullptr, &k);
+      if (k >= 1) set.push_back(act[i].h), in_batch.push_back(i);
+    }
     if (set != bt_set) {
       if (bt) bm_batch_destroy(bt);
       bt = nullptr;
-      if (bm_batch_create(set.data(), (int32_t)set.size(), &bt) != BM_OK) bt = nullptr;
+      if (!set.empty() && bm_batch_create(set.data(), (int32_t)set.size(), &bt) != BM_OK) bt = nullptr;
       bt_set = set;
     }
-    std::vector<double> Fb(act.size(), NAN);
+    std::vector<double> Fb(set.size(), NAN);
     std::vector<bm_status> sts(act.size(), BM_OK);
     if (bt) {
       const bm_status st = bm_batch_bm_phase(bt, 3, Fb.data());
-      if (st != BM_OK) std::fill(sts.begin(), sts.end(), st);
+      if (st != BM_OK)
+        for (size_t i : in_batch) sts[i] = st;
     }
     // PG steps concurrently, each solve on its own stream
     std::atomic<size_t> next{0};
