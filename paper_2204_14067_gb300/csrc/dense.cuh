@@ -34,7 +34,7 @@ void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, 
 // Sparse part of Z products: Out(i,:) += gamma * sum_e v_e X(idx_e,:) over a
 // segment split (CSR: i = row, idx = col; CSC: i = col, idx = row).  Blocks
 // wider than kSpmmCols run as several launches over column slices.
-constexpr int kSpmmCols = 144;
+constexpr int kSpmmCols = 256;
 void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall& Out, float gamma);
 
 // Accuracy modes of the symmetric eigensolver.

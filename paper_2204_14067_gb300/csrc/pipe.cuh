@@ -415,14 +415,15 @@ __device__ __forceinline__ float4 gather4(const float* g, const void* gb, int64_
 }
 
 // Lanes that share one entry (its row split into float4 chunks l, l + L, ...)
-// and resident blocks per SM, by pass mode: the line-search pass (two
-// gathered rows, three dot products) runs fastest with eight lanes per entry
-// and four blocks per SM, the single-gather passes with four lanes and three
-// blocks (measured on the recommendation-scale workload at k = 64).
+// and resident blocks per SM, by pass mode: the loss/gradient pass runs
+// fastest with four lanes per entry and three blocks per SM; the line-search
+// pass (two gathered rows, three dot products) and the q-wide SpMM (up to
+// 2 (k_max + 1) columns) with eight lanes and four blocks (measured on the
+// recommendation-scale workload at k = 64).
 template <int MODE>
-constexpr int lanes_per_entry() { return MODE == 2 ? 8 : 4; }
+constexpr int lanes_per_entry() { return MODE == 0 ? 4 : 8; }
 template <int MODE>
-constexpr int direct_blocks_per_sm() { return MODE == 2 ? 4 : 3; }
+constexpr int direct_blocks_per_sm() { return MODE == 0 ? 3 : 4; }
 
 // One segment s of a pass (the warp's lanes cooperate).  EX: the row width is
 // exactly 4 V chunks of 4 floats, so no chunk needs a bounds test.
@@ -684,13 +685,6 @@ void launch_pipe(const PipeArgs& a, cudaStream_t st, bool bf = false) {
       BM_DIRECT_CASE(8)
       default:
         break;
-    }
-    if constexpr (MODE == 1) {   // the PG step's products with Z^T reach 2 (k_max + 1) columns
-      if (V == 9) {
-        if (bf) k_direct<MODE, 9, true, false><<<grid, 256, 0, st>>>(a);
-        else k_direct<MODE, 9, false, false><<<grid, 256, 0, st>>>(a);
-        return;
-      }
     }
     throw Error{BM_ERR_INVALID, "sparse pass: too many columns"};
 #undef BM_DIRECT_CASE

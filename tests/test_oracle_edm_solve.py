@@ -1,0 +1,121 @@
+"""Pins of the distance-geometry QSDP oracle (oracle/edm_oracle.py) against
+facts independent of it: the variational inequality of a projection onto a
+convex set (Lemma "PiX"), dense operators, finite differences, brute-force
+line search, the exact operator norm, the dense exact PG step, and the dense
+convex optimum of the QSDP."""
+import numpy as np
+import pytest
+
+from oracle import bm_oracle as O
+from oracle import edm_oracle as E
+from synth import self_avoiding_chain
+
+
+def _chain(n, seed):
+    p = self_avoiding_chain(n=n, seed=seed)
+    i, j, d, w = E.pair_arrays(p.i, p.j, p.d, 1.0)
+    return p, i, j, d, w
+
+
+def test_projection_is_the_euclidean_projection_onto_the_feasible_set():
+    rng = np.random.default_rng(0)
+    n = 25
+    A = rng.standard_normal((n, n))
+    G = A + A.T
+    P = E.dense_project(G)
+    assert np.linalg.eigvalsh(P).min() >= -1e-10
+    assert np.abs(P @ np.ones(n)).max() <= 1e-10
+    J = np.eye(n) - np.ones((n, n)) / n
+    for _ in range(20):
+        M = rng.standard_normal((n, rng.integers(1, n)))
+        Y = J @ M @ M.T @ J                       # a feasible point
+        # <G - P, Y - P> <= 0 characterises the projection onto a convex set
+        assert np.sum((G - P) * (Y - P)) <= 1e-9 * (1 + np.abs(G).sum())
+
+
+def test_laplacian_apply_matches_dense_sum_of_E_ij():
+    rng = np.random.default_rng(1)
+    n, npairs = 12, 30
+    i = rng.integers(0, n, npairs)
+    j = (i + rng.integers(1, n, npairs)) % n
+    c = rng.standard_normal(npairs)
+    U = rng.standard_normal((n, 3))
+    L = np.zeros((n, n))
+    for a, b, cc in zip(i, j, c):
+        e = np.zeros(n)
+        e[a], e[b] = 1.0, -1.0
+        L += cc * np.outer(e, e)
+    assert np.allclose(E.laplacian_apply(n, i, j, c, U), L @ U, atol=1e-12)
+
+
+def test_gradient_and_line_search_quartic():
+    p, i, j, d, w = _chain(40, 11)
+    rng = np.random.default_rng(2)
+    lam = O.edm_lambda(p.n, d)
+    V = E.center(p.X_true @ rng.standard_normal((3, 4)) * 0.5 + 0.1 * rng.standard_normal((p.n, 4)))
+    g = E.gradient(V, i, j, d, w, lam)
+    h = 1e-6
+    for _ in range(5):
+        a, b = rng.integers(0, p.n), rng.integers(0, 4)
+        Vp, Vm = V.copy(), V.copy()
+        Vp[a, b] += h
+        Vm[a, b] -= h
+        fd = (E.objective(Vp, i, j, d, w, lam) - E.objective(Vm, i, j, d, w, lam)) / (2 * h)
+        assert abs(fd - g[a, b]) <= 1e-6 * (1 + abs(g).max())
+    D = E.center(rng.standard_normal(V.shape))
+    c = E.line_search_coeffs(V, D, i, j, d, w, lam)
+    for s in (0.0, 0.3, -0.7, 1.9):
+        poly = sum(c[q] * s ** q for q in range(5))
+        assert abs(poly - E.objective(V + s * D, i, j, d, w, lam)) <= 1e-9 * (1 + abs(poly))
+    V2, F = E.bm_phase(V, i, j, d, w, lam, 6)
+    assert all(b <= a * (1 + 1e-12) + 1e-12 for a, b in zip(F, F[1:]))
+    assert np.abs(V2.sum(axis=0)).max() <= 1e-9
+
+
+def test_lipschitz_bound_dominates_the_operator_norm():
+    p, i, j, d, w = _chain(30, 12)
+    n = p.n
+    w = np.random.default_rng(3).uniform(0.5, 2.0, i.shape[0])
+    # A(X)_p = sqrt(w_p) <E_p, X>: ||A* A|| = lambda_max of the Gram of sqrt(w_p) vec(E_p)
+    rows = []
+    for a, b, ww in zip(i, j, w):
+        e = np.zeros(n)
+        e[a], e[b] = 1.0, -1.0
+        rows.append(np.sqrt(ww) * np.outer(e, e).ravel())
+    M = np.array(rows)
+    exact = np.linalg.eigvalsh(M @ M.T).max()
+    bound = E.lipschitz(n, i, j, w)
+    assert bound >= exact * (1 - 1e-12)
+    assert bound <= 4.0 * exact
+
+
+def test_pg_step_equals_dense_exact_projection():
+    p, i, j, d, w = _chain(40, 13)
+    n = p.n
+    lam = O.edm_lambda(n, d)
+    alpha = 1.0 / E.lipschitz(n, i, j, w)
+    rng = np.random.default_rng(4)
+    V = E.center(p.X_true @ rng.standard_normal((3, 5)) * 0.7)
+    V, _ = E.bm_phase(V, i, j, d, w, lam, 4)
+    X = V @ V.T
+    Xd = E.dense_project(X - alpha * (E.dense_grad_f(X, i, j, d, w) + lam * np.eye(n)))
+    rpos = int(np.sum(np.linalg.eigvalsh(Xd) > 1e-9 * np.abs(Xd).max()))
+    opt = O.Options(lmsvd_tol=1e-14, lmsvd_imax=400)
+    st = E.EdmState(V=V, U=np.zeros((n, 0)), k_eig=rpos + 3)
+    st2, info = E.prox_step(st, i, j, d, w, lam, alpha, 40, opt)
+    assert info.rank == rpos
+    Xn = st2.V @ st2.V.T
+    assert np.linalg.norm(Xn - Xd) <= 1e-7 * np.linalg.norm(Xd)
+
+
+def test_solve_reaches_the_dense_convex_optimum():
+    n = 30
+    p, i, j, d, w = _chain(n, 17)
+    lam = O.edm_lambda(n, d)
+    X_star, F_star = E.dense_solve(n, i, j, d, w, lam)
+    st, F, ranks = E.solve(n, i, j, d, w, lam, 30, O.Options(lmsvd_tol=1e-12, lmsvd_imax=200),
+                           max_outer=300, tol=1e-14)
+    assert abs(F[-1] - F_star) <= 1e-6 * abs(F_star)
+    ev = np.linalg.eigvalsh(X_star)
+    assert ranks[-1] == int(np.sum(ev > 1e-6 * ev.max()))
+    assert np.abs(st.V.sum(axis=0)).max() <= 1e-8
