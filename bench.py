@@ -10,6 +10,8 @@ second per cycle (nnz / cycle time) summed over replicas.
 `--mode grad` times bm_loss_grad alone (the SDDMM + two SpMM passes).
 `--mode tto` times a solve to the FP64 oracle's objective on the planted
 500 x 300 problem; `--mode serve` measures the continuous-batching server.
+`--mode edm` times the distance-geometry loss/gradient and `--mode edm_solve`
+the cycles of Algorithm 1 on the distance-geometry QSDP (30,000-point chain).
 `--impl reference` times the FP64 oracle on the host cores on a bounded
 sample of the same workload.
 """
@@ -591,6 +593,144 @@ def run_edm(args):
     }
 
 
+def edm_solve_bytes(kernel, n, npairs, ld, q):
+    """Algorithmic bytes of one launch of the distance-geometry solve kernels
+    (every pair is stored in both directions: 2 * npairs directed entries).
+
+    edm_pass: column index + d^2 per entry (8 B), V read and gradient write
+              (n * ld * 4 each), residual write (4 B per entry) when the PG
+              step asks for it (counted here: the bench's cycle asks for it
+              once per PG step, the BM iterations do not; the smaller figure
+              is used).
+    edm_ls:   column index + d^2 per entry (8 B), V and D read (n * ld * 4 each).
+    edm_lap:  column index + coefficient per entry (8 B), block read once
+              (n * q * 4), output read + write (2 * n * q * 4).
+    """
+    E = 2 * npairs
+    if kernel == "edm_pass":
+        return E * 8 + 2 * n * ld * 4
+    if kernel == "edm_ls":
+        return E * 8 + 2 * n * ld * 4
+    if kernel == "edm_lap":
+        return E * 8 + 3 * n * q * 4
+    return None
+
+
+def run_edm_solve(args):
+    """Algorithm 1 on the distance-geometry QSDP, the 30,000-point chain
+    (about 450,000 pairs within 6.0), k_max = 16: one step = one cycle of
+    30 BM iterations (PR+ with the exact quartic line search) and one inexact
+    PG step (LmSVD on Z + sigma J, projection, rank rule).  The initial PG step
+    from X = 0 and W warm-up cycles run before the timed region."""
+    import torch
+
+    import paper_2204_14067_gb300 as B
+    from synth import self_avoiding_chain
+
+    p = self_avoiding_chain(n=30_000, seed=3)
+    k_max, epochs = 16, 30
+    lam = -10.0 * np.sqrt(p.n) / float(np.sum(p.d.astype(np.float64) ** 2))   # lambda of the conformation workload
+    h = B.bm_edm_create(p.n, p.i, p.j, p.d, lam, k_max)
+    o = B.bm_default_options()
+    o.bm_epochs = epochs
+    B.bm_edm_set_options(h, o)
+    stream = torch.cuda.Stream()
+    B.bm_edm_set_stream(h, stream)
+    t0 = time.perf_counter()
+    init = B.bm_edm_init(h)
+    init_s = time.perf_counter() - t0
+    F_hist = [init["F"]]
+
+    def cycle():
+        B.bm_edm_bm_phase(h, epochs)
+        return B.bm_edm_prox_step(h)
+
+    for _ in range(args.warmup):
+        F_hist.append(cycle()["F"])
+    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_edm_solve.csv")
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    sampler, fh = _clock_sampler(clk_path)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos.append(cycle())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if sampler is not None:
+        sampler.terminate()
+        sampler.wait()
+        fh.close()
+    clocks = _clock_summary(clk_path, 0)
+    F_hist += [x["F"] for x in infos]
+    # kernel breakdown of the same cycles (events around every launch)
+    B.bm_edm_profile_enable(h, True)
+    for _ in range(args.steps):
+        cycle()
+    prof = B.bm_edm_profile_read(h)
+    B.bm_edm_profile_enable(h, False)
+    k_now = B.bm_edm_get_factor(h, p.n).shape[1]
+    # end to end through the public API with host buffers: factor in, one cycle, factor out
+    Vh = np.ascontiguousarray(B.bm_edm_get_factor(h, p.n))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        B.bm_edm_set_factor(h, Vh.shape[1], Vh)
+        cycle()
+        Vh = np.ascontiguousarray(B.bm_edm_get_factor(h, p.n))
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    B.bm_edm_destroy(h)
+
+    pairs = p.npairs
+    ld = max(4, (k_now + 3) // 4 * 4)
+    q = 2 * (k_max + 1)
+    peaks, kind = _load_peaks()
+    modeled = {nm: v for nm, v in prof.items() if edm_solve_bytes(nm, p.n, pairs, ld, q) is not None}
+    top = max(modeled.items(), key=lambda kv: kv[1][1])[0] if modeled else None
+    roof = None
+    if top is not None:
+        launches, tot = prof[top]
+        by = edm_solve_bytes(top, p.n, pairs, ld, q if top != "edm_lap" else min(q, 128))
+        avg = tot / max(1, launches)
+        ach = by / (avg / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": top, "achieved": ach, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": ach / float(peaks["hbm_gbs"]), "traffic": None, "peak_source": kind,
+                "bytes_per_launch": by, "avg_launch_ms": avg,
+                "note": "the problem (about 30 MB) is L2-resident; bytes are the algorithmic DRAM figure"}
+    cpu = None
+    if not args.no_cpu:
+        from oracle import bm_oracle as O
+        from oracle import edm_oracle as E
+        i, j, d, w = E.pair_arrays(p.i, p.j, p.d, 1.0)
+        alpha = 1.0 / E.lipschitz(p.n, i, j, w)
+        V = Vh.astype(np.float64)
+        st = E.EdmState(V=V, U=np.zeros((p.n, 0)), k_eig=min(k_max, V.shape[1] + 1))
+        t0 = time.perf_counter()
+        Vb, _ = E.bm_phase(st.V, i, j, d, w, lam, epochs)
+        E.prox_step(E.EdmState(V=Vb, U=st.U, k_eig=st.k_eig), i, j, d, w, lam, alpha, k_max, O.Options())
+        el = time.perf_counter() - t0
+        cpu = {"value": 1.0 / el, "unit": "cycles/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one cycle of the same workload from the GPU's last factor, {el:.1f} s"}
+    return {
+        "metric": "EDM Algorithm 1 cycles/s", "value": 1e3 / ms, "unit": "cycles/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"3-D self-avoiding chain, n = {p.n}, {pairs} pairs within 6.0, k_max = {k_max}",
+                   "step": f"{epochs} BM iterations + 1 inexact PG step", "lambda": lam,
+                   "l2": "problem fits in L2 (about 30 MB): cached between steps", "k_end": k_now,
+                   "init_s": init_s, "F": [F_hist[0], F_hist[-1]],
+                   "lmsvd_iters": [x["lmsvd_iters"] for x in infos], "ranks": [x["rank"] for x in infos]},
+        "e2e": {"value": 1.0 / e2e_s, "unit": "cycles/s", "h2d_bytes_per_step": int(Vh.nbytes),
+                "d2h_bytes_per_step": int(Vh.nbytes)},
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "kernels": {kname: {"launches": v[0], "ms": round(v[1], 4)} for kname, v in sorted(prof.items())},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+
+
 def _dist_cpu():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return None, int(os.environ.get("RANK", "0")), ws
@@ -602,7 +742,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="cycle", choices=["cycle", "grad", "tto", "serve", "edm"])
+    ap.add_argument("--mode", default="cycle", choices=["cycle", "grad", "tto", "serve", "edm", "edm_solve"])
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="1: BF16 copies of the gathered factor rows (cycle and grad modes)")
     ap.add_argument("--serve-count", type=int, default=24)
@@ -620,6 +760,8 @@ def main():
         line = run_serve(args)
     elif args.mode == "edm":
         line = run_edm(args)
+    elif args.mode == "edm_solve":
+        line = run_edm_solve(args)
     else:
         line = run_ours(args)
     if line is not None:

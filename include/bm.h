@@ -352,6 +352,52 @@ bm_status bm_edm_loss_grad(bm_edm_handle h, double* g, float* gV);
 bm_status bm_edm_set_stream(bm_edm_handle h, void* stream);
 
 /*
+ * Algorithm 1 on the distance-geometry QSDP (Eq. "QSDP": minimise
+ * 1/2 sum w_ij (X_ii + X_jj - 2 X_ij - d_ij^2)^2 + lambda <I, X> over X
+ * positive semidefinite with <E, X> = 0), factored as X = V V^T, V^T e = 0
+ * (Eq. "EDM").  BM phase: Polak-Ribiere+ with the exact quartic line search
+ * (every direction keeps V^T e = 0).  PG step: by Lemma "PiX" and
+ * Eq. "proxsym", X+ = P_S+(V V^T - alpha L_{w r} - alpha lambda J) with
+ * L_c = sum c_ij E_ij, J = I - e e^T / n, alpha = 1/L (Gershgorin bound of
+ * ||A* A||); the leading eigenpairs come from LmSVD (Algorithm 2) on the
+ * operator shifted to be positive semidefinite; V+ = U diag(sqrt(mu_+)).
+ * Rank rule: k eigenpairs are computed; all positive -> the next step
+ * computes k + floor(n / 20) (at most k_max), else the number of positive
+ * ones.  The initial point is one PG step from X = 0 with
+ * k_0 = min(100, floor(0.15 n), k_max) pairs.
+ *
+ * The factor (bm_edm_set_factor or a PG step) is expected to satisfy
+ * V^T e = 0; setting a factor forgets the warm start and the rank schedule,
+ * and the next PG step then computes min(k + 1, k_max) eigenpairs.
+ *
+ * bm_edm_set_options: bm_epochs, lmsvd_p (0 or 1), lmsvd_imax,
+ *   lmsvd_min_iter, lmsvd_tol, tau and seed of *o are used (defaults:
+ *   bm_default_options).
+ * bm_edm_init: the initial PG step (the factor becomes X_0's).
+ * bm_edm_bm_phase: `epochs` BM iterations; *F (nullable) = g(V) after them.
+ * bm_edm_prox_step: one PG step; info (nullable): k_new = rank of X+,
+ *   warm_cols = eigenpairs computed, lmsvd_iters, n_L = eigenpairs the next
+ *   step computes, cap_hit = 1 if all computed eigenvalues were positive,
+ *   eps = the shift sigma, F = g(V+).
+ * bm_edm_solve: bm_edm_init if the factor is empty, then cycles of bm_epochs
+ *   BM iterations and one PG step until |F_t - F_{t-1}| / (1 + |F_{t-1}|) <
+ *   tol, F <= F_target (if nonzero) or max_outer / time_limit_s
+ *   (BM_ERR_NOT_CONVERGED).
+ * bm_edm_get_factor: *k (nullable) = rank; V (nullable, n x k row-major,
+ *   host or device) = the factor.
+ */
+bm_status bm_edm_set_options(bm_edm_handle h, const bm_options* o);
+bm_status bm_edm_init(bm_edm_handle h, bm_prox_info* info);
+bm_status bm_edm_bm_phase(bm_edm_handle h, int32_t epochs, double* F);
+bm_status bm_edm_prox_step(bm_edm_handle h, bm_prox_info* info);
+bm_status bm_edm_solve(bm_edm_handle h, const bm_solve_opts* o, bm_solve_info* info);
+bm_status bm_edm_get_factor(bm_edm_handle h, int32_t* k, float* V);
+/* Kernel timing of the handle's launches, as bm_profile_enable / bm_profile_read. */
+bm_status bm_edm_profile_enable(bm_edm_handle h, int32_t enable);
+bm_status bm_edm_profile_read(bm_edm_handle h, int32_t cap, char* names, int64_t* launches, double* total_ms,
+                              int32_t* count);
+
+/*
  * bm_loss_grad_csr_noalloc -- the loss and W-side gradient of (MF) for
  * callers that cannot allocate device memory.  The paper has no counterpart;
  * this exists for code that may not call cudaMalloc where it needs a

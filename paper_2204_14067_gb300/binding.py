@@ -304,6 +304,14 @@ _SIGS.update({
     "bm_edm_set_factor": (_c.c_int, [_P, _c.c_int32, _P]),
     "bm_edm_loss_grad": (_c.c_int, [_P, _P, _P]),
     "bm_edm_set_stream": (_c.c_int, [_P, _P]),
+    "bm_edm_set_options": (_c.c_int, [_P, _c.POINTER(bm_options)]),
+    "bm_edm_init": (_c.c_int, [_P, _c.POINTER(bm_prox_info)]),
+    "bm_edm_bm_phase": (_c.c_int, [_P, _c.c_int32, _c.POINTER(_c.c_double)]),
+    "bm_edm_prox_step": (_c.c_int, [_P, _c.POINTER(bm_prox_info)]),
+    "bm_edm_solve": (_c.c_int, [_P, _c.POINTER(bm_solve_opts), _c.POINTER(bm_solve_info)]),
+    "bm_edm_get_factor": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _P]),
+    "bm_edm_profile_enable": (_c.c_int, [_P, _c.c_int32]),
+    "bm_edm_profile_read": (_c.c_int, [_P, _c.c_int32, _P, _P, _P, _c.POINTER(_c.c_int32)]),
 })
 
 
@@ -326,6 +334,71 @@ def bm_edm_destroy(h):
 
 def bm_edm_set_factor(h, k, V):
     _check_edm(lib().bm_edm_set_factor(h, int(k), _ptr(V)), h)
+
+
+def _edm_info(info: bm_prox_info):
+    return {"rank": info.k_new, "computed": info.warm_cols, "lmsvd_iters": info.lmsvd_iters,
+            "k_next": info.n_L, "all_positive": bool(info.cap_hit), "sigma": info.eps, "F": info.F}
+
+
+def bm_edm_set_options(h, o: bm_options):
+    _check_edm(lib().bm_edm_set_options(h, ctypes.byref(o)), h)
+
+
+def bm_edm_init(h):
+    info = bm_prox_info()
+    _check_edm(lib().bm_edm_init(h, ctypes.byref(info)), h)
+    return _edm_info(info)
+
+
+def bm_edm_bm_phase(h, epochs):
+    F = ctypes.c_double()
+    _check_edm(lib().bm_edm_bm_phase(h, int(epochs), ctypes.byref(F)), h)
+    return F.value
+
+
+def bm_edm_prox_step(h):
+    info = bm_prox_info()
+    _check_edm(lib().bm_edm_prox_step(h, ctypes.byref(info)), h)
+    return _edm_info(info)
+
+
+def bm_edm_solve(h, max_outer=100, tol=1e-10, F_target=0.0, time_limit_s=0.0):
+    o = bm_solve_opts(max_outer=int(max_outer), tol=float(tol), F_target=float(F_target),
+                      time_limit_s=float(time_limit_s))
+    info = bm_solve_info()
+    st = lib().bm_edm_solve(h, ctypes.byref(o), ctypes.byref(info))
+    if st not in (BM_OK, BM_ERR_NOT_CONVERGED):
+        _check_edm(st, h)
+    return {"outer": info.outer, "k": info.k, "converged": bool(info.converged), "F": info.F,
+            "seconds": info.seconds}
+
+
+def bm_edm_get_factor(h, n):
+    kk = ctypes.c_int32()
+    _check_edm(lib().bm_edm_get_factor(h, ctypes.byref(kk), None), h)
+    V = np.zeros((n, kk.value), np.float32)
+    if kk.value:
+        _check_edm(lib().bm_edm_get_factor(h, None, _ptr(V)), h)
+    return V
+
+
+def bm_edm_profile_enable(h, enable=True):
+    _check_edm(lib().bm_edm_profile_enable(h, 1 if enable else 0), h)
+
+
+def bm_edm_profile_read(h, cap=64):
+    """{kernel name: (launches, total_ms)} since the last bm_edm_profile_enable."""
+    names = ctypes.create_string_buffer(48 * cap)
+    launches = np.zeros(cap, np.int64)
+    ms = np.zeros(cap, np.float64)
+    cnt = ctypes.c_int32()
+    _check_edm(lib().bm_edm_profile_read(h, cap, names, _ptr(launches), _ptr(ms), ctypes.byref(cnt)), h)
+    out = {}
+    for i in range(min(cnt.value, cap)):
+        nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out
 
 
 def bm_edm_set_stream(h, stream):

@@ -240,6 +240,33 @@ double bm_phase_dev(bm_ctx& h, int epochs, double* F_out) {
 
 using namespace bm;
 
+namespace bm {
+void profile_report(Profiler& prof, int32_t cap, char* names, int64_t* launches, double* total_ms,
+                    int32_t* count) {
+  std::vector<std::string> keys;
+  std::vector<int64_t> cnt;
+  std::vector<double> ms;
+  for (auto& mk : prof.marks) {
+    if (!mk.second.second) continue;
+    float t = 0.f;
+    BM_CUDA(cudaEventElapsedTime(&t, mk.second.first, mk.second.second));
+    size_t i = 0;
+    while (i < keys.size() && keys[i] != mk.first) ++i;
+    if (i == keys.size()) keys.push_back(mk.first), cnt.push_back(0), ms.push_back(0.0);
+    cnt[i] += 1;
+    ms[i] += t;
+  }
+  if (count) *count = (int32_t)keys.size();
+  for (size_t i = 0; i < keys.size() && (int32_t)i < cap; ++i) {
+    if (names) {
+      std::snprintf(names + 48 * i, 48, "%s", keys[i].c_str());
+    }
+    if (launches) launches[i] = cnt[i];
+    if (total_ms) total_ms[i] = ms[i];
+  }
+}
+}  // namespace bm
+
 extern "C" {
 
 bm_status bm_default_options(bm_options* o) {
@@ -605,27 +632,7 @@ bm_status bm_profile_read(bm_handle h, int32_t cap, char* names, int64_t* launch
   if (!h) return BM_ERR_INVALID;
   return guarded(h, [&] {
     BM_CUDA(cudaStreamSynchronize(h->stream));
-    std::vector<std::string> keys;
-    std::vector<int64_t> cnt;
-    std::vector<double> ms;
-    for (auto& mk : h->prof.marks) {
-      if (!mk.second.second) continue;
-      float t = 0.f;
-      BM_CUDA(cudaEventElapsedTime(&t, mk.second.first, mk.second.second));
-      size_t i = 0;
-      while (i < keys.size() && keys[i] != mk.first) ++i;
-      if (i == keys.size()) keys.push_back(mk.first), cnt.push_back(0), ms.push_back(0.0);
-      cnt[i] += 1;
-      ms[i] += t;
-    }
-    if (count) *count = (int32_t)keys.size();
-    for (size_t i = 0; i < keys.size() && (int32_t)i < cap; ++i) {
-      if (names) {
-        std::snprintf(names + 48 * i, 48, "%s", keys[i].c_str());
-      }
-      if (launches) launches[i] = cnt[i];
-      if (total_ms) total_ms[i] = ms[i];
-    }
+    profile_report(h->prof, cap, names, launches, total_ms, count);
   });
 }
 
@@ -634,5 +641,6 @@ bm_status bm_profile_read(bm_handle h, int32_t cap, char* names, int64_t* launch
 namespace bm {
 // exported for prox.cu
 void set_rank_ext(bm_ctx& h, int k) { set_rank(h, k); }
+double quartic_argmin_ext(const double c[5]) { return quartic_argmin(c); }
 double objective_ext(bm_ctx& h) { return objective_now(h); }
 }  // namespace bm

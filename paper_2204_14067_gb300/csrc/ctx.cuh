@@ -199,6 +199,11 @@ void xpby_dev(bm_ctx& h, float* y, const float* x, float b, int64_t count);     
 void copy_pad_dev(bm_ctx& h, float* dst, int ldd, const float* src, int lds, int64_t rows,
                   int cols, cudaMemcpyKind kind);
 
+// api.cu: argmin over s >= 0 of c0 + c1 s + ... + c4 s^4 (0 or a real root of the derivative)
+// Per-name launch counts and device milliseconds of the recorded marks (synchronise first).
+void profile_report(Profiler& prof, int32_t cap, char* names, int64_t* launches, double* total_ms, int32_t* count);
+double quartic_argmin_ext(const double c[5]);
+
 // prox.cu
 void prox_create(bm_ctx& h);
 void prox_destroy(bm_ctx& h);

@@ -7,22 +7,8 @@
 #include <algorithm>
 #include <cmath>
 
-#include "ctx.cuh"
+#include "edm.cuh"
 
-struct bm_edm_ctx {
-  int64_t n = 0, npairs = 0;
-  double lambda = 0;
-  int k_max = 0, k = 0, ld = 4;
-  cudaStream_t stream = nullptr;      // stream the calls run on
-  cudaStream_t own_stream = nullptr;  // the handle's own stream
-  bm::DevBuf<int64_t> row_ptr;
-  bm::DevBuf<int32_t> col;
-  bm::DevBuf<float> dsq, w;    // d_ij^2 and w_ij in CSR order
-  bm::Segs seg;
-  bm::DevBuf<float> V, gV, partial;
-  bm::DevBuf<double> fseg, red;
-  std::string err;
-};
 
 namespace bm {
 namespace {
@@ -87,6 +73,7 @@ struct EdmArgs {
   float* out;
   float* partial;
   double* fseg;
+  float* r_out;     // nullable: residual per directed entry
 };
 
 // Four lanes per directed entry, V float4 chunks per lane.
@@ -140,7 +127,10 @@ __global__ void __launch_bounds__(256) k_edm_pass(EdmArgs a) {
           acc[v].z = fmaf(cw, df[v].z, acc[v].z);
           acc[v].w = fmaf(cw, df[v].w, acc[v].w);
         }
-        if (l == 0) fs = fmaf(0.25f * ww * r, r, fs);  // each pair appears twice
+        if (l == 0) {
+          fs = fmaf(0.25f * ww * r, r, fs);  // each pair appears twice
+          if (a.r_out && ok) a.r_out[e0 + src] = r;
+        }
       }
     }
 #pragma unroll
@@ -191,13 +181,35 @@ __global__ void k_edm_fixup(const int32_t* __restrict__ mrow, const int32_t* __r
   }
 }
 
-// g = sum of segment partials + lam ||V||^2 (deterministic, one block)
-__global__ void k_edm_total(const double* __restrict__ fseg, int64_t nseg, const float* __restrict__ V, int64_t nv,
-                            double lam, double* __restrict__ out) {
-  __shared__ double sh[1024];
+// g = sum of segment partials + lam ||V||^2, in two deterministic stages:
+// block b sums a fixed strided share into part[b], then one block adds the
+// parts in order.
+constexpr int kTotalThreads = 256;
+__global__ void __launch_bounds__(kTotalThreads) k_edm_total_part(const double* __restrict__ fseg, int64_t nseg,
+                                                                 const float* __restrict__ V, int64_t nv, double lam,
+                                                                 double* __restrict__ part) {
+  __shared__ double sh[kTotalThreads];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < nseg; i += blockDim.x) s += fseg[i];
-  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) s += lam * (double)V[i] * (double)V[i];
+  for (int64_t i = t0; i < nseg; i += stride) s += fseg[i];
+  float q = 0.f;   // FP32 partial of ||V||^2 over this thread's few entries
+  for (int64_t i = t0; i < nv; i += stride) q = fmaf(V[i], V[i], q);
+  s += lam * (double)q;
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kTotalThreads) k_edm_total_final(const double* __restrict__ part, int nparts,
+                                                                  double* __restrict__ out) {
+  __shared__ double sh[kTotalThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
@@ -206,6 +218,8 @@ __global__ void k_edm_total(const double* __restrict__ fseg, int64_t nseg, const
   }
   if (threadIdx.x == 0) out[0] = sh[0];
 }
+
+int total_parts() { return std::max(1, std::min(1024, 2 * num_sms())); }
 
 template <int VC>
 void launch_edm(const EdmArgs& a, cudaStream_t st) {
@@ -310,8 +324,14 @@ bm_status bm_edm_create(int64_t n, int64_t npairs, const int32_t* i, const int32
     h->gV.alloc((size_t)n * ldmax);
     h->partial.alloc((size_t)std::max<int64_t>(1, h->seg.nslots) * ldmax);
     h->fseg.alloc(std::max<int64_t>(1, h->seg.nseg));
-    h->red.alloc(4);
+    h->red.alloc(total_parts() + 1);
     BM_CUDA(cudaMemsetAsync(h->V.get(), 0, (size_t)n * ldmax * sizeof(float), s));
+    // the dense routines of the solve run on the handle's stream with this scratch
+    bm_default_options(&h->opt);
+    h->core.stream = h->stream;
+    BM_CUDA(cudaGetDevice(&h->core.device));
+    h->core.sc.red.alloc(4096);
+    h->core.sc.scal.alloc(64);
     BM_CUDA(cudaStreamSynchronize(s));
   });
   if (st != BM_OK) {
@@ -349,6 +369,7 @@ bm_status bm_edm_set_factor(bm_edm_handle h, int32_t k, const float* V) {
     BM_REQUIRE(V, BM_ERR_INVALID, "bm_edm_set_factor: NULL factor");
     h->k = k;
     h->ld = round_up4(k);
+    bm::edm_solve_reset(h->ss);
     BM_CUDA(cudaMemsetAsync(h->V.get(), 0, (size_t)h->n * h->ld * sizeof(float), h->stream));
     BM_CUDA(cudaMemcpy2DAsync(h->V.get(), h->ld * sizeof(float), V, k * sizeof(float), k * sizeof(float), h->n,
                               is_device_ptr(V) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
@@ -360,56 +381,79 @@ bm_status bm_edm_loss_grad(bm_edm_handle h, double* g, float* gV) {
   if (!h) return BM_ERR_INVALID;
   return edm_guarded(h, [&] {
     BM_REQUIRE(h->k >= 1, BM_ERR_INVALID, "bm_edm_loss_grad: set a factor first");
-    EdmArgs a;
-    a.seg_row = h->seg.row.get();
-    a.seg_beg = h->seg.beg.get();
-    a.seg_end = h->seg.end.get();
-    a.seg_slot = h->seg.slot.get();
-    a.nseg = h->seg.nseg;
-    a.col = h->col.get();
-    a.dsq = h->dsq.get();
-    a.w = h->w.get();
-    a.V = h->V.get();
-    a.ld = h->ld;
-    a.nchunk = h->ld / 4;
-    a.lam = (float)h->lambda;
-    a.out = h->gV.get();
-    a.partial = h->partial.get();
-    a.fseg = h->fseg.get();
-    const int VC = std::max(1, (a.nchunk + 3) / 4);
-    switch (VC) {
-      case 1: launch_edm<1>(a, h->stream); break;
-      case 2: launch_edm<2>(a, h->stream); break;
-      case 3: launch_edm<3>(a, h->stream); break;
-      case 4: launch_edm<4>(a, h->stream); break;
-      case 5: launch_edm<5>(a, h->stream); break;
-      case 6: launch_edm<6>(a, h->stream); break;
-      case 7: launch_edm<7>(a, h->stream); break;
-      case 8: launch_edm<8>(a, h->stream); break;
-      default: throw Error{BM_ERR_INVALID, "bm_edm_loss_grad: k above 128"};
-    }
-    BM_CHECK_LAUNCH();
-    if (h->seg.nmulti) {
-      const int64_t work = h->seg.nmulti * h->ld;
-      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), num_sms() * 8));
-      k_edm_fixup<<<grid, 256, 0, h->stream>>>(h->seg.mrow.get(), h->seg.mfirst.get(), h->seg.mcount.get(),
-                                               h->seg.nmulti, h->partial.get(), h->V.get(), h->ld, a.lam, a.out);
-      BM_CHECK_LAUNCH();
-    }
-    k_edm_total<<<1, 1024, 0, h->stream>>>(h->fseg.get(), h->seg.nseg, h->V.get(), h->n * (int64_t)h->ld,
-                                           h->lambda, h->red.get());
-    BM_CHECK_LAUNCH();
-    double gv = 0;
-    BM_CUDA(cudaMemcpyAsync(&gv, h->red.get(), sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    const double gv = edm_loss_grad_dev(*h, gV != nullptr, nullptr);
     if (gV) {
       BM_CUDA(cudaMemcpy2DAsync(gV, h->k * sizeof(float), h->gV.get(), h->ld * sizeof(float), h->k * sizeof(float),
                                 h->n, is_device_ptr(gV) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 h->stream));
+      BM_CUDA(cudaStreamSynchronize(h->stream));
     }
-    BM_CUDA(cudaStreamSynchronize(h->stream));
-    BM_REQUIRE(std::isfinite(gv), BM_ERR_NUMERIC, "bm_edm_loss_grad: loss is not finite");
     if (g) *g = gv;
   });
 }
 
 }  // extern "C"
+
+namespace bm {
+
+double edm_loss_grad_dev(bm_edm_ctx& hh, bool want_grad, float* r_out) {
+  bm_edm_ctx* h = &hh;
+  EdmArgs a;
+  a.seg_row = h->seg.row.get();
+  a.seg_beg = h->seg.beg.get();
+  a.seg_end = h->seg.end.get();
+  a.seg_slot = h->seg.slot.get();
+  a.nseg = h->seg.nseg;
+  a.col = h->col.get();
+  a.dsq = h->dsq.get();
+  a.w = h->w.get();
+  a.V = h->V.get();
+  a.ld = h->ld;
+  a.nchunk = h->ld / 4;
+  a.lam = (float)h->lambda;
+  a.out = h->gV.get();
+  a.partial = h->partial.get();
+  a.fseg = h->fseg.get();
+  a.r_out = r_out;
+  const int VC = std::max(1, (a.nchunk + 3) / 4);
+  bm_ctx& cx = h->core;
+  cx.stream = h->stream;
+  if (cx.prof.on) cx.prof.begin("edm_pass", h->stream);
+  switch (VC) {
+    case 1: launch_edm<1>(a, h->stream); break;
+    case 2: launch_edm<2>(a, h->stream); break;
+    case 3: launch_edm<3>(a, h->stream); break;
+    case 4: launch_edm<4>(a, h->stream); break;
+    case 5: launch_edm<5>(a, h->stream); break;
+    case 6: launch_edm<6>(a, h->stream); break;
+    case 7: launch_edm<7>(a, h->stream); break;
+    case 8: launch_edm<8>(a, h->stream); break;
+    default: throw Error{BM_ERR_INVALID, "distance-geometry pass: k above 128"};
+  }
+  BM_CHECK_LAUNCH();
+  if (cx.prof.on) cx.prof.end(h->stream);
+  if (h->seg.nmulti) {
+    const int64_t work = h->seg.nmulti * h->ld;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), num_sms() * 8));
+    BM_LAUNCH(cx, "edm_fixup",
+              k_edm_fixup<<<grid, 256, 0, h->stream>>>(h->seg.mrow.get(), h->seg.mfirst.get(), h->seg.mcount.get(),
+                                                       h->seg.nmulti, h->partial.get(), h->V.get(), h->ld, a.lam,
+                                                       a.out));
+  }
+  (void)want_grad;
+  const int parts = total_parts();
+  BM_REQUIRE((int64_t)h->red.n >= parts + 1, BM_ERR_INVALID, "distance-geometry pass: reduction buffer too small");
+  BM_LAUNCH(cx, "edm_total",
+            k_edm_total_part<<<parts, kTotalThreads, 0, h->stream>>>(h->fseg.get(), h->seg.nseg, h->V.get(),
+                                                                      h->n * (int64_t)h->ld, h->lambda,
+                                                                      h->red.get() + 1));
+  BM_LAUNCH(cx, "edm_total",
+            k_edm_total_final<<<1, kTotalThreads, 0, h->stream>>>(h->red.get() + 1, parts, h->red.get()));
+  double gv = 0;
+  BM_CUDA(cudaMemcpyAsync(&gv, h->red.get(), sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  BM_CUDA(cudaStreamSynchronize(h->stream));
+  BM_REQUIRE(std::isfinite(gv), BM_ERR_NUMERIC, "distance-geometry loss is not finite");
+  return gv;
+}
+
+}  // namespace bm
