@@ -427,11 +427,13 @@ def run_tto(args):
     F_star, rank = _read_golden_tiny()
     p = named_config("tiny")
     target = F_star * (1 + 1e-6)
+    opts = B.bm_default_options()
+    opts.step_rule = args.step_rule
     runs = []
     for rep in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 64)
+        h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 64, opts)
         t1 = time.perf_counter()
         r = B.bm_solve(h, max_outer=2000, tol=0.0, F_target=target)
         torch.cuda.synchronize()
@@ -448,14 +450,22 @@ def run_tto(args):
         from oracle import bm_oracle as O
         ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
         t0 = time.perf_counter()
-        _, oi = O.solve(ix, p.lam, 8, 64, O.Options(), max_outer=2000, tol=0.0, F_target=target)
+        if args.step_rule == 1:
+            from oracle import sparsa_oracle as S
+            _, Fh, _ = S.solve_bb(ix, p.lam, 8, 64, O.Options(), S.BbOptions(), max_outer=2000, tol=0.0,
+                                  F_target=target)
+            cycles = len(Fh) - 1
+        else:
+            _, oi = O.solve(ix, p.lam, 8, 64, O.Options(), max_outer=2000, tol=0.0, F_target=target)
+            cycles = oi.outer
         cpu = {"value": time.perf_counter() - t0, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"the same solve to the same target ({oi.outer} cycles)"}
+               "sample": f"the same solve to the same target ({cycles} cycles)"}
     return {
         "metric": "time to oracle objective (relative 1e-6)", "value": solve_s, "unit": "s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "planted rank-5 500x300, 15,000 entries, lambda 0.5, k0 8, k_max 64",
+                   "step_rule": "SpaRSA (BB + backtracking)" if args.step_rule == 1 else "fixed alpha 1.99",
                    "F_star": F_star, "oracle_rank": rank, "cycles": [x[2] for x in runs],
                    "converged": all(x[4] for x in runs), "final_rel": max((x[3] - F_star) / F_star for x in runs)},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(p.nnz * 12),
@@ -746,6 +756,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="1: BF16 copies of the gathered factor rows (cycle and grad modes)")
     ap.add_argument("--serve-count", type=int, default=24)
+    ap.add_argument("--step-rule", type=int, default=0, choices=[0, 1],
+                    help="tto mode: 0 fixed PG step, 1 SpaRSA step rule")
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the natural work split (one panel)")

@@ -66,7 +66,8 @@ typedef struct {
   int32_t precision;     /* 0: FP32 factors; 1: BF16 factor copies for the gathers */
   uint64_t seed;         /* counter-based RNG key for the sketch and xi_t */
   int32_t autotune;      /* 1: bm_solve runs bm_autotune once before its first cycle; 0 */
-  int32_t pad_;
+  int32_t step_rule;     /* PG step size in bm_solve: 0 fixed alpha; 1 the SpaRSA rule of
+                            bm_prox_step_bb (supplement Sec. "The SpaRSA variant"); 0 */
 } bm_options;
 
 /* Result of one inexact PG step (Eq. "inexactpg", "truncate"). */
@@ -430,6 +431,47 @@ bm_status bm_loss_grad_csr_noalloc(int64_t m, int64_t n, const int64_t* row_ptr,
                                    const float* val, const float* W, const float* H, int32_t k, int32_t ld,
                                    double lambda, float* gW, double* f, void* stream);
 const char* bm_noalloc_last_error(void);
+
+/*
+ * The SpaRSA step rule for the PG step (supplement Sec. "The SpaRSA variant
+ * for Matrix Completion").  alpha_BB of Eq. "proxBB" from the last two points
+ * X~_{t-1}, X~_t at which a PG step was taken, read as the step length
+ * ||dX||_F^2 / <dX, dG> (the printed ratio is its reciprocal, a curvature),
+ * with <dX, dG> = ||r_t - r_{t-1}||^2 over Omega and ||dX||_F^2 from k x k
+ * Grams (Eq. "trace" with its last term's sign corrected), clipped to
+ * [alpha_min, alpha_max]; the first step (no previous point, or after
+ * bm_set_factors / bm_set_state) starts from bm_options.alpha, clipped alike.  Then the
+ * smallest i >= 0 such that alpha = alpha_BB beta^i gives an X_{t+1}
+ * satisfying Eq. "back" or Eq. "decrease" (delta); each rejected trial
+ * restores X~_t and the warm-start / safeguard state exactly.  After
+ * max_backtracks reductions the last trial is kept (accepted_by = 0).
+ *   bm_bb_default_options: alpha_min 1e-3, alpha_max 1e3, beta 0.5,
+ *     delta 0.995, max_backtracks 30.
+ *   bm_set_bb_options: BM_ERR_INVALID unless 0 < alpha_min <= alpha_max
+ *     (finite), beta and delta in (0, 1), max_backtracks >= 0.
+ *   bm_prox_step_bb: info (nullable) as bm_prox_step, F = F(X_{t+1});
+ *     bb (nullable) receives the step record.
+ * Device memory: two extra copies of the factors and two residual arrays.
+ */
+typedef struct {
+  double alpha_min;
+  double alpha_max;
+  double beta;
+  double delta;
+  int32_t max_backtracks;
+  int32_t pad_;
+} bm_bb_options;
+
+typedef struct {
+  double alpha_bb;       /* Eq. "proxBB" value before backtracking */
+  double alpha;          /* step length taken */
+  int32_t backtracks;    /* reductions by beta */
+  int32_t accepted_by;   /* 1 Eq. "back", 2 Eq. "decrease" only, 0 none within max_backtracks */
+} bm_bb_info;
+
+bm_status bm_bb_default_options(bm_bb_options* o);
+bm_status bm_set_bb_options(bm_handle h, const bm_bb_options* o);
+bm_status bm_prox_step_bb(bm_handle h, bm_prox_info* info, bm_bb_info* bb);
 
 /*
  * Kernel timing for measurement.  While enabled, the library records a pair

@@ -34,7 +34,17 @@ class bm_options(ctypes.Structure):
                 ("lmsvd_p", ctypes.c_int32), ("lmsvd_imax", ctypes.c_int32), ("lmsvd_min_iter", ctypes.c_int32),
                 ("lmsvd_tol", ctypes.c_double), ("tau", ctypes.c_double), ("ritz_rel", ctypes.c_double),
                 ("psi0", ctypes.c_double), ("k_init", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("autotune", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("autotune", ctypes.c_int32), ("step_rule", ctypes.c_int32)]
+
+
+class bm_bb_options(ctypes.Structure):
+    _fields_ = [("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double), ("beta", ctypes.c_double),
+                ("delta", ctypes.c_double), ("max_backtracks", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class bm_bb_info(ctypes.Structure):
+    _fields_ = [("alpha_bb", ctypes.c_double), ("alpha", ctypes.c_double), ("backtracks", ctypes.c_int32),
+                ("accepted_by", ctypes.c_int32)]
 
 
 BM_PASS_KINDS = 5
@@ -81,6 +91,9 @@ _SIGS = {
     "bm_bm_phase": (_c.c_int, [_P, _c.c_int32, _P]),
     "bm_init": (_c.c_int, [_P, _c.POINTER(bm_prox_info)]),
     "bm_prox_step": (_c.c_int, [_P, _c.c_double, _c.POINTER(bm_prox_info)]),
+    "bm_bb_default_options": (_c.c_int, [_c.POINTER(bm_bb_options)]),
+    "bm_set_bb_options": (_c.c_int, [_P, _c.POINTER(bm_bb_options)]),
+    "bm_prox_step_bb": (_c.c_int, [_P, _c.POINTER(bm_prox_info), _c.POINTER(bm_bb_info)]),
     "bm_solve": (_c.c_int, [_P, _c.POINTER(bm_solve_opts), _c.POINTER(bm_solve_info)]),
     "bm_profile_enable": (_c.c_int, [_P, _c.c_int32]),
     "bm_autotune": (_c.c_int, [_P, _c.c_int32, _c.POINTER(bm_tune_info)]),
@@ -231,6 +244,25 @@ def bm_prox_step(h, alpha=0.0):
     info = bm_prox_info()
     _check(lib().bm_prox_step(h, float(alpha), ctypes.byref(info)), h)
     return _info_dict(info)
+
+
+def bm_bb_default_options() -> bm_bb_options:
+    o = bm_bb_options()
+    _check(lib().bm_bb_default_options(ctypes.byref(o)))
+    return o
+
+
+def bm_set_bb_options(h, o: bm_bb_options):
+    _check(lib().bm_set_bb_options(h, ctypes.byref(o)), h)
+
+
+def bm_prox_step_bb(h):
+    """One PG step with the SpaRSA step rule: (prox info dict, step record dict)."""
+    info = bm_prox_info()
+    bb = bm_bb_info()
+    _check(lib().bm_prox_step_bb(h, ctypes.byref(info), ctypes.byref(bb)), h)
+    return _info_dict(info), {"alpha_bb": bb.alpha_bb, "alpha": bb.alpha, "backtracks": bb.backtracks,
+                              "accepted_by": bb.accepted_by}
 
 
 def bm_solve(h, max_outer=100, tol=1e-10, F_target=0.0, time_limit_s=0.0, raise_not_converged=False):

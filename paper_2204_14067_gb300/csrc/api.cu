@@ -284,6 +284,7 @@ bm_status bm_default_options(bm_options* o) {
   o->k_init = 8;
   o->precision = 0;
   o->autotune = 0;
+  o->step_rule = 0;
   o->seed = 0;
   return BM_OK;
 }
@@ -310,6 +311,7 @@ bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, cons
     BM_REQUIRE(o.alpha > 0 && std::isfinite(o.alpha), BM_ERR_INVALID, "bm_create: alpha must be > 0");
     BM_REQUIRE(o.lmsvd_p >= 0 && o.lmsvd_p <= 1, BM_ERR_INVALID, "bm_create: lmsvd_p must be 0 or 1");
     BM_REQUIRE(o.precision == 0 || o.precision == 1, BM_ERR_INVALID, "bm_create: precision must be 0 or 1");
+    BM_REQUIRE(o.step_rule == 0 || o.step_rule == 1, BM_ERR_INVALID, "bm_create: step_rule must be 0 or 1");
     BM_REQUIRE(o.lmsvd_imax >= 1 && o.k_init >= 1 && o.bm_epochs >= 0 && o.pg_steps >= 0, BM_ERR_INVALID,
                "bm_create: iteration counts out of range");
     h = new bm_ctx();
@@ -361,6 +363,8 @@ void bm_destroy(bm_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   prox_destroy(*h);
+  bb_destroy(h->bb);
+  h->bb = nullptr;
   cudaStream_t own = h->own_stream;
   delete h;
   if (own) cudaStreamDestroy(own);
@@ -591,7 +595,12 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
       if (so.F_target > 0 && F_bm <= so.F_target) { converged = true; ended_on_bm = true; break; }
       F_prev = F;
       have_prev = true;
-      for (int x = 0; x < h->opt.pg_steps; ++x) prox_step_dev(*h, h->opt.alpha, nullptr);
+      for (int x = 0; x < h->opt.pg_steps; ++x) {
+        if (h->opt.step_rule == 1)
+          prox_step_bb_dev(*h, nullptr, nullptr);
+        else
+          prox_step_dev(*h, h->opt.alpha, nullptr);
+      }
       if (so.time_limit_s > 0 && elapsed() > so.time_limit_s) { ++outer; break; }
     }
     (void)ended_on_bm;

@@ -81,6 +81,7 @@ struct Scratch {
 };
 
 struct ProxState;  // defined in prox.cu
+struct BbState;    // defined in sparsa.cu (SpaRSA step rule)
 
 // Optional per-kernel event timing (bm_profile_enable).
 struct Profiler {
@@ -115,6 +116,7 @@ struct bm_ctx {
   bm::DevBuf<float> r_csr, r_csc;  // residual R on Omega in CSR / CSC order
   bm::Scratch sc;
   bm::ProxState* ps = nullptr;
+  bm::BbState* bb = nullptr;     // SpaRSA step-rule state (created on first use)
   bm::Profiler prof;
   std::string err;
   bool bm_changed = false;       // BM phase moved since the last PG step
@@ -208,7 +210,12 @@ double quartic_argmin_ext(const double c[5]);
 void prox_create(bm_ctx& h);
 void prox_destroy(bm_ctx& h);
 void prox_reset(bm_ctx& h);
-void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info);
+// One inexact PG step with step size alpha; info->F (an extra loss pass) only with eval_F.
+void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info, bool eval_F = true);
+// One PG step with the SpaRSA step rule (sparsa.cu); bb_reset forgets the previous point.
+void prox_step_bb_dev(bm_ctx& h, bm_prox_info* info, bm_bb_info* bb);
+void bb_reset(bm_ctx& h);
+void bb_destroy(BbState* s);
 void init_step_dev(bm_ctx& h, bm_prox_info* info);
 // Checkpoint of the PG-step state (warm start and safeguard): size, save
 // into host memory, load from host memory (validated; BM_ERR_INVALID).

@@ -396,7 +396,7 @@ bm_status bm_edm_loss_grad(bm_edm_handle h, double* g, float* gV) {
 
 namespace bm {
 
-double edm_loss_grad_dev(bm_edm_ctx& hh, bool want_grad, float* r_out) {
+double edm_loss_grad_dev(bm_edm_ctx& hh, bool want_grad, float* r_out, bool sync) {
   bm_edm_ctx* h = &hh;
   EdmArgs a;
   a.seg_row = h->seg.row.get();
@@ -449,6 +449,7 @@ double edm_loss_grad_dev(bm_edm_ctx& hh, bool want_grad, float* r_out) {
                                                                       h->red.get() + 1));
   BM_LAUNCH(cx, "edm_total",
             k_edm_total_final<<<1, kTotalThreads, 0, h->stream>>>(h->red.get() + 1, parts, h->red.get()));
+  if (!sync) return std::nan("");
   double gv = 0;
   BM_CUDA(cudaMemcpyAsync(&gv, h->red.get(), sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   BM_CUDA(cudaStreamSynchronize(h->stream));

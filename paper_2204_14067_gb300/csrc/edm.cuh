@@ -33,6 +33,7 @@ struct bm_edm_ctx {
 namespace bm {
 // g(V) of Eq. "EDM" at the current factor; with want_grad the gradient goes
 // to h.gV; with r_out the residual r_ij = ||v_i - v_j||^2 - d_ij^2 of every
-// directed entry (CSR order).  Returns after a stream synchronisation.
-double edm_loss_grad_dev(bm_edm_ctx& h, bool want_grad, float* r_out);
+// directed entry (CSR order).  Returns after a stream synchronisation; with
+// sync = false it returns NaN at once and g(V) is left in h.red[0].
+double edm_loss_grad_dev(bm_edm_ctx& h, bool want_grad, float* r_out, bool sync = true);
 }  // namespace bm

@@ -33,6 +33,7 @@ struct EdmSolveState {
   DevBuf<float> D, gp;     // BM direction, previous gradient (n x ld)
   DevBuf<double> G, E, ev, colsum;
   DevBuf<double> rowbuf, segsums, sums4;   // per-row bounds, line-search partials
+  DevBuf<double> dotpart, scal;            // dot-product partials; 8 scalars read back per sync
   DevBuf<float> Ts;
   double alpha = 0, sigma = 0;
   int ku = 0;              // columns of U_t in blk[kUp]
@@ -259,6 +260,53 @@ __global__ void __launch_bounds__(kSumThreads) k_sum4_part(const double* __restr
     __syncthreads();
   }
   if (threadIdx.x < 4) part[4 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// part[2 b + q] = sum over a fixed strided share of x_q . y_q (q = 0, 1; float4 chunks)
+__global__ void __launch_bounds__(kSumThreads) k_dots2_part(const float4* __restrict__ x0,
+                                                           const float4* __restrict__ y0,
+                                                           const float4* __restrict__ x1,
+                                                           const float4* __restrict__ y1, int64_t n4,
+                                                           double* __restrict__ part) {
+  __shared__ double sh[2][kSumThreads];
+  float a0 = 0.f, a1 = 0.f;   // a thread sums only a few chunks; FP64 across threads
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 u = x0[i], v = y0[i], p = x1[i], q = y1[i];
+    a0 = fmaf(u.x, v.x, fmaf(u.y, v.y, fmaf(u.z, v.z, fmaf(u.w, v.w, a0))));
+    a1 = fmaf(p.x, q.x, fmaf(p.y, q.y, fmaf(p.z, q.z, fmaf(p.w, q.w, a1))));
+  }
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) part[2 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kSumThreads) k_dots2_final(const double* __restrict__ part, int parts,
+                                                            double* __restrict__ out) {
+  __shared__ double sh[2][kSumThreads];
+  double a0 = 0.0, a1 = 0.0;
+  for (int i = threadIdx.x; i < parts; i += blockDim.x) {
+    a0 += part[2 * i];
+    a1 += part[2 * i + 1];
+  }
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // coef_e = alpha w_e r_e (r_e of the directed entry; r_e = -d_e^2 when V = 0)
@@ -607,6 +655,8 @@ void ensure_state(bm_edm_ctx& h) {
   s->rowbuf.alloc(std::max<int64_t>(h.n, 1));
   s->segsums.alloc(4 * std::max<int64_t>(1, h.seg.nseg));
   s->sums4.alloc(4 * (sum_parts() + 1));
+  s->dotpart.alloc(2 * (size_t)sum_parts());
+  s->scal.alloc(8);
   // SpMM partial rows up to 128 columns
   const int64_t need = std::max<int64_t>(1, h.seg.nslots) * 128;
   if ((int64_t)h.partial.n < need) {
@@ -700,7 +750,17 @@ EdmStepOut init_step(bm_edm_ctx& h) {
   return o;
 }
 
-double dot(bm_edm_ctx& h, const float* x, const float* y) { return dot_dev(core(h), x, y, h.n * (int64_t)h.ld); }
+// launch (x0 . y0, x1 . y1) over the n x ld factor layout into out[0..1] (device); no synchronisation
+void dots2(bm_edm_ctx& h, const float* x0, const float* y0, const float* x1, const float* y1, double* out) {
+  EdmSolveState& s = *h.ss;
+  const int parts = sum_parts();
+  const int64_t n4 = h.n * (int64_t)h.ld / 4;
+  BM_LAUNCH(core(h), "edm_dots", k_dots2_part<<<parts, kSumThreads, 0, h.stream>>>(
+                                     reinterpret_cast<const float4*>(x0), reinterpret_cast<const float4*>(y0),
+                                     reinterpret_cast<const float4*>(x1), reinterpret_cast<const float4*>(y1), n4,
+                                     s.dotpart.get()));
+  BM_LAUNCH(core(h), "edm_dots", k_dots2_final<<<1, kSumThreads, 0, h.stream>>>(s.dotpart.get(), parts, out));
+}
 
 // Polak-Ribiere+ with the exact quartic line search; returns F after the last iteration
 double bm_phase(bm_edm_ctx& h, int epochs) {
@@ -708,17 +768,10 @@ double bm_phase(bm_edm_ctx& h, int epochs) {
   bm_ctx& cx = core(h);
   if (h.k == 0 || epochs <= 0) return edm_loss_grad_dev(h, false, nullptr);
   const int64_t cnt = h.n * (int64_t)h.ld;
-  double F = 0.0, gg_prev = 0.0;
-  bool have_prev = false;
-  for (int e = 0; e < epochs; ++e) {
-    F = edm_loss_grad_dev(h, true, nullptr);
-    const double gg = dot(h, h.gV.get(), h.gV.get());
-    double beta = 0.0;
-    if (have_prev && gg_prev > 0) beta = std::max(0.0, (gg - dot(h, h.gV.get(), s.gp.get())) / gg_prev);
-    if (!have_prev) BM_CUDA(cudaMemsetAsync(s.D.get(), 0, cnt * sizeof(float), h.stream));
-    xpby_dev(cx, s.D.get(), h.gV.get(), (float)beta, cnt);   // D = -g + beta D
-    if (beta > 0 && dot(h, s.D.get(), h.gV.get()) >= 0) xpby_dev(cx, s.D.get(), h.gV.get(), 0.f, cnt);
-    // quartic coefficients (each pair appears twice among the directed entries)
+  double* sc = s.scal.get();
+  // quartic coefficients of g(V + s D): the line-search sums (each pair appears
+  // twice among the directed entries) and <g, D>, <D, D>, read back in one sync
+  auto quartic = [&](double F, double c[5]) {
     PairArgs a{};
     a.seg_row = h.seg.row.get();
     a.seg_beg = h.seg.beg.get();
@@ -748,14 +801,37 @@ double bm_phase(bm_edm_ctx& h, int epochs) {
     const int parts = sum_parts();
     BM_LAUNCH(cx, "edm_sum4", k_sum4_part<<<parts, kSumThreads, 0, h.stream>>>(s.segsums.get(), a.nseg,
                                                                                  s.sums4.get() + 4));
-    BM_LAUNCH(cx, "edm_sum4", k_sum4_part<<<1, kSumThreads, 0, h.stream>>>(s.sums4.get() + 4, parts, s.sums4.get()));
-    std::vector<double> S = d2h(h, s.sums4.get(), 4);
-    double c[5];
+    BM_LAUNCH(cx, "edm_sum4", k_sum4_part<<<1, kSumThreads, 0, h.stream>>>(s.sums4.get() + 4, parts, sc + 4));
+    dots2(h, h.gV.get(), s.D.get(), s.D.get(), s.D.get(), sc + 2);
+    std::vector<double> v = d2h(h, sc + 2, 6);   // <g, D>, <D, D>, S1..S4
     c[0] = F;
-    c[1] = dot(h, h.gV.get(), s.D.get());                       // <grad g, D>
-    c[2] = 0.25 * S[1] + h.lambda * dot(h, s.D.get(), s.D.get());
-    c[3] = 0.5 * S[2];
-    c[4] = 0.25 * S[3];
+    c[1] = v[0];                                 // <grad g, D>
+    c[2] = 0.25 * v[3] + h.lambda * v[1];
+    c[3] = 0.5 * v[4];
+    c[4] = 0.25 * v[5];
+  };
+  double F = 0.0, gg_prev = 0.0;
+  bool have_prev = false;
+  for (int e = 0; e < epochs; ++e) {
+    edm_loss_grad_dev(h, true, nullptr, false);
+    dots2(h, h.gV.get(), h.gV.get(), h.gV.get(), have_prev ? s.gp.get() : h.gV.get(), sc);
+    double head[3];
+    BM_CUDA(cudaMemcpyAsync(head, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+    BM_CUDA(cudaMemcpyAsync(head + 2, h.red.get(), sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+    BM_CUDA(cudaStreamSynchronize(h.stream));
+    F = head[2];
+    BM_REQUIRE(std::isfinite(F), BM_ERR_NUMERIC, "distance-geometry loss is not finite");
+    const double gg = head[0];
+    double beta = 0.0;
+    if (have_prev && gg_prev > 0) beta = std::max(0.0, (gg - head[1]) / gg_prev);
+    if (!have_prev) BM_CUDA(cudaMemsetAsync(s.D.get(), 0, cnt * sizeof(float), h.stream));
+    xpby_dev(cx, s.D.get(), h.gV.get(), (float)beta, cnt);   // D = -g + beta D
+    double c[5];
+    quartic(F, c);
+    if (beta > 0 && c[1] >= 0) {   // not a descent direction: restart with D = -g
+      xpby_dev(cx, s.D.get(), h.gV.get(), 0.f, cnt);
+      quartic(F, c);
+    }
     const double st = quartic_argmin_ext(c);
     if (st > 0) {
       axpy_dev(cx, h.V.get(), s.D.get(), (float)st, cnt);

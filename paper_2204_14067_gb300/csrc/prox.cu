@@ -456,9 +456,10 @@ void prox_reset(bm_ctx& h) {
   ps.rank_cur = h.k;
   ps.prev_warm = h.k + 1;
   ps.t = 0;
+  bb_reset(h);
 }
 
-void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info) {
+void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info, bool eval_F) {
   ProxState& ps = *h.ps;
   const bm_options& o = h.opt;
   const int m = (int)h.ix.m;
@@ -535,7 +536,7 @@ void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info) {
   ps.prev_warm = warm;
   ps.t += 1;
   h.bm_changed = false;
-  const double F = info ? objective_ext(h) : 0.0;
+  const double F = (info && eval_F) ? objective_ext(h) : 0.0;
   fill_info(info, s, warm, l, F);
 }
 

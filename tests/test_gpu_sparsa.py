@@ -1,0 +1,144 @@
+"""GPU parity of the SpaRSA step rule (supplement Sec. "The SpaRSA variant for
+Matrix Completion") against the FP64 oracle in oracle/sparsa_oracle.py: the
+Barzilai-Borwein value of Eq. "proxBB", the backtracking count and which of
+Eq. "back" / Eq. "decrease" accepted the step, the rank and the objective
+after every PG step of a few cycles; and Algorithm 1 with the SpaRSA rule
+reaching the oracle's optimal value."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import bm_oracle as O
+from oracle import sparsa_oracle as S
+from synth import named_config, random_factors
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def B():
+    import paper_2204_14067_gb300 as B
+    B.lib()
+    return B
+
+
+def _opts(B, **kw):
+    o = B.bm_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _oracle_opts(o):
+    return O.Options(alpha=o.alpha, lmsvd_p=o.lmsvd_p, lmsvd_imax=o.lmsvd_imax, lmsvd_tol=o.lmsvd_tol,
+                     lmsvd_min_iter=o.lmsvd_min_iter, tau=o.tau, ritz_rel=o.ritz_rel, psi0=o.psi0,
+                     seed=o.seed, bm_epochs=o.bm_epochs, pg_steps=o.pg_steps)
+
+
+def _internal(ix, W, H):
+    W, H = W.astype(np.float64), H.astype(np.float64)
+    return (H, W) if ix.transposed else (W, H)
+
+
+def _state(ix, W, H, opt):
+    U0, _ = O.orth(W, tau=1e-12)
+    k = W.shape[1]
+    return O.State(W=W, H=H, U_prev=U0, U_prev2=None, u=None, psi=opt.psi0, rank_hist=[k, k],
+                   prev_warm_cols=k + 1, t=0, bm_changed=True)
+
+
+@pytest.mark.parametrize("case", ["tiny", "zipf_t"])
+def test_bb_steps_match_oracle(B, case):
+    if case == "tiny":
+        p = named_config("tiny")
+        k = 6
+    else:
+        p = named_config("small", m=4000, n=900, nnz=180_000, seed=12)     # stored transposed
+        k = 9
+    o = _opts(B, lmsvd_tol=0.0, lmsvd_imax=8)
+    h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 30, o)
+    ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
+    oo = _oracle_opts(o)
+    bo = S.BbOptions()
+    try:
+        W, H = random_factors(p.m, p.n, k, seed=4, scale=0.3)
+        B.bm_set_factors(h, k, W, H)
+        Wi, Hi = _internal(ix, W, H)
+        st = _state(ix, Wi, Hi, oo)
+        prev = None
+        backtracked = False
+        for t in range(4):
+            B.bm_bm_phase(h, 3)
+            info, bb = B.bm_prox_step_bb(h)
+            st, _ = O.bm_phase(ix, st, p.lam, 3)
+            if t == 0:
+                # after bm_set_factors the library takes U_t = orth(W) of the
+                # factors the first PG step sees (here: after the BM phase)
+                st.U_prev = O.orth(st.W, tau=1e-12)[0]
+            st, oinfo, obb, prev = S.prox_step_bb(ix, st, p.lam, 30, oo, bo, prev)
+            ctx = (t, bb, obb)
+            assert abs(bb["alpha_bb"] - obb.alpha_bb) <= 1e-4 * obb.alpha_bb, ctx
+            assert bb["backtracks"] == obb.backtracks, ctx
+            assert bb["accepted_by"] == obb.accepted_by, ctx
+            assert abs(bb["alpha"] - obb.alpha) <= 1e-4 * obb.alpha, ctx
+            assert info["k_new"] == oinfo.k_new, ctx
+            Fo = O.objective(ix, st.W, st.H, p.lam)
+            assert abs(info["F"] - Fo) <= 1e-5 * Fo, ctx
+            backtracked = backtracked or obb.backtracks > 0
+        assert backtracked   # the cases exercise the restore path
+    finally:
+        B.bm_destroy(h)
+
+
+def test_sparsa_solve_reaches_the_oracle_optimum(B):
+    """Algorithm 1 with the SpaRSA step on the 500 x 300 planted problem
+    (lambda = 0.5, k0 = 8): the convex optimum's value, written by
+    tests/golden/make_tiny_optimum.py from the fixed-step oracle solve, is
+    reached within 1e-6 (the optimum does not depend on the step rule)."""
+    F_star = None
+    for line in open(os.path.join(GOLDEN, "tiny_optimum.txt")):
+        if line.startswith("F_star"):
+            F_star = float(line.split()[1])
+    p = named_config("tiny")
+    o = _opts(B, step_rule=1)
+    h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 64, o)
+    try:
+        r = B.bm_solve(h, max_outer=400, tol=0.0, F_target=F_star * (1 + 1e-6))
+        assert r["converged"], r
+        ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
+        Wg, Hg = B.bm_get_factors(h, p.m, p.n)
+        Wi, Hi = _internal(ix, Wg, Hg)
+        F_chk = O.objective(ix, Wi, Hi, p.lam)
+        assert F_star * (1 - 1e-7) <= F_chk <= F_star * (1 + 2e-6)
+    finally:
+        B.bm_destroy(h)
+
+
+def test_bb_options_are_validated(B):
+    p = named_config("tiny")
+    h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 16, _opts(B))
+    try:
+        o = B.bm_bb_default_options()
+        assert (o.alpha_min, o.alpha_max, o.beta, o.delta, o.max_backtracks) == (1e-3, 1e3, 0.5, 0.995, 30)
+        for field, bad in (("beta", 1.0), ("delta", 0.0), ("alpha_min", 0.0), ("max_backtracks", -1)):
+            b = B.bm_bb_default_options()
+            setattr(b, field, bad)
+            with pytest.raises(B.BMError):
+                B.bm_set_bb_options(h, b)
+        b = B.bm_bb_default_options()
+        b.alpha_max = 1.0
+        B.bm_set_bb_options(h, b)
+        B.bm_init(h)
+        for _ in range(3):
+            B.bm_bm_phase(h, 3)
+            _, bb = B.bm_prox_step_bb(h)
+            # alpha <= 1/L = 1: Eq. "decrease" holds at the first trial
+            assert bb["backtracks"] == 0 and bb["accepted_by"] in (1, 2)
+            assert bb["alpha"] <= 1.0
+    finally:
+        B.bm_destroy(h)
+    with pytest.raises(B.BMError):
+        B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 16, _opts(B, step_rule=2))
