@@ -106,22 +106,23 @@ def _sumall(dist, x):
     return float(t.item())
 
 
-def algorithmic_bytes(kernel, d, k, q):
+def algorithmic_bytes(kernel, d, k, q, vb=4):
     """Algorithmic DRAM bytes of one launch (unique data each launch must move).
 
-    grad_csr: col idx + value per entry (8 B), residual write (4 B), W read,
-              gW write (m*k*4 each), H read once (n*k*4).
-    grad_csc: row idx + value (8 B), residual write (4 B), H read, gH write,
-              W read once.
+    grad_csr: col idx + value per entry (4 + vb B; vb = 1 with the one-byte
+              value codec, else 4), residual write (4 B), W read, gW write
+              (m*k*4 each), H read once (n*k*4).
+    grad_csc: row idx + value (4 + vb B), residual write (4 B), H read, gH
+              write, W read once.
     linesearch_csr: col idx + residual (8 B), W, DW (m*k*4 each), H, DH (n*k*4 each).
     spmm_csc / spmm_csr (prox): idx + residual value (8 B), gathered block
               read once (rows*q*4), output read + write (2*rows*q*4).
     """
     m, n, nnz = d["m"], d["n"], d["nnz"]
     if kernel == "grad_csr":
-        return nnz * 12 + (2 * m + n) * k * 4
+        return nnz * (8 + vb) + (2 * m + n) * k * 4
     if kernel == "grad_csc":
-        return nnz * 12 + (2 * n + m) * k * 4
+        return nnz * (8 + vb) + (2 * n + m) * k * 4
     if kernel == "linesearch_csr":
         return nnz * 8 + 2 * (m + n) * k * 4
     if kernel == "spmm_csc":
@@ -131,21 +132,24 @@ def algorithmic_bytes(kernel, d, k, q):
     return None
 
 
-def measured_traffic(kernel, d, k, panels=1):
+def measured_traffic(kernel, d, k, panels=1, codec=False):
     """DRAM bytes per launch of `kernel` from a committed ncu summary
-    (profiles/<kernel>_netflix_k<k>.txt: 'dram_bytes_per_launch: N' taken with
-    'panels: P'), or None when no capture of the kernel as it runs exists."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_netflix_k{k}.txt")
-    got, cap_panels = None, None
+    (profiles/<kernel>_netflix_k<k>[_codec].txt: 'dram_bytes_per_launch: N'
+    taken with 'panels: P'), or None when no capture of the kernel as it runs
+    exists."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_netflix_k{k}{'_codec' if codec else ''}.txt")
+    got, cap_panels, cap_codec = None, None, 0
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_launch:"):
                 got = float(line.split(":", 1)[1])
             elif line.startswith("panels:"):
                 cap_panels = int(line.split(":", 1)[1])
+            elif line.startswith("value_codec:"):
+                cap_codec = int(line.split(":", 1)[1])
     except OSError:
         return None
-    return got if cap_panels == panels else None
+    return got if cap_panels == panels and cap_codec == int(codec) else None
 
 
 def algorithmic_flops(kernel, d, k, q):
@@ -173,7 +177,9 @@ def run_ours(args):
     t_gen = time.time() - t_gen
     opt = B.bm_default_options()
     opt.precision = args.precision
+    opt.value_codec = args.codec
     h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, p.k_max, opt)
+    codec_on = B.bm_get_codes(h)[0]
     stream = torch.cuda.Stream()
     B.bm_set_stream(h, stream)
     d = B.bm_dims(h)
@@ -254,7 +260,7 @@ def run_ours(args):
     q = k_now + 1
     kk = k_now if args.mode == "cycle" else k
     fl = algorithmic_flops(name, d, kk, q) if name else None
-    by = algorithmic_bytes(name, d, kk, q) if name else None
+    by = algorithmic_bytes(name, d, kk, q, 1 if codec_on else 4) if name else None
     avg_s = (tot_ms / launches) / 1e3 if launches else None
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock, TFLOP/s
@@ -262,7 +268,8 @@ def run_ours(args):
     if avg_s and fl is not None and by is not None:
         intensity = fl / by
         ridge = alu_peak * 1e12 / (float(peaks["hbm_gbs"]) * 1e9)
-        traffic = measured_traffic(name, d, kk, tune[name][0] if tune and name in tune else 1)
+        traffic = measured_traffic(name, d, kk, tune[name][0] if tune and name in tune else 1,
+                                   codec_on and name in ("grad_csr", "grad_csc"))
         if intensity >= ridge:
             ach = fl / avg_s / 1e12
             roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
@@ -298,6 +305,7 @@ def run_ours(args):
                    if args.mode == "cycle" else "one loss/gradient evaluation",
                    "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (1.6 GB of index per pass)",
                    "generate_s": round(t_gen, 1),
+                   "value_codec": "one byte per observed value" if codec_on else "fp32 values",
                    "panels": ({nm: v[0] for nm, v in tune.items()} if tune else "natural split")},
         "e2e": {"value": e2e_val, "unit": "nnz/s",
                 "h2d_bytes_per_step": int(W0.nbytes + H0.nbytes),
@@ -756,6 +764,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="1: BF16 copies of the gathered factor rows (cycle and grad modes)")
     ap.add_argument("--serve-count", type=int, default=24)
+    ap.add_argument("--codec", type=int, default=1, choices=[0, 1],
+                    help="1: one-byte codes for integer observed values in the loss/gradient passes")
     ap.add_argument("--step-rule", type=int, default=0, choices=[0, 1],
                     help="tto mode: 0 fixed PG step, 1 SpaRSA step rule")
     ap.add_argument("--config", default=WORKLOAD)

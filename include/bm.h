@@ -68,6 +68,10 @@ typedef struct {
   int32_t autotune;      /* 1: bm_solve runs bm_autotune once before its first cycle; 0 */
   int32_t step_rule;     /* PG step size in bm_solve: 0 fixed alpha; 1 the SpaRSA rule of
                             bm_prox_step_bb (supplement Sec. "The SpaRSA variant"); 0 */
+  int32_t value_codec;   /* 1: when every observed value is an integer and they span at most
+                            255, the loss/gradient passes read one byte per entry
+                            (a = code + offset, exact); 0: always FP32 values; 1 */
+  int32_t pad_;
 } bm_options;
 
 /* Result of one inexact PG step (Eq. "inexactpg", "truncate"). */
@@ -148,6 +152,14 @@ bm_status bm_dims(bm_handle h, int64_t* m, int64_t* n, int64_t* nnz, int32_t* tr
  */
 bm_status bm_get_index(bm_handle h, int64_t* row_ptr, int32_t* col, float* val, int64_t* col_ptr,
                        int32_t* row, float* cval, int64_t* csr2csc);
+
+/*
+ * bm_get_codes -- the value codec (bm_options.value_codec): *active = 1 if
+ * the loss/gradient passes read one-byte codes, *offset the integer added to
+ * a code; csr_codes / csc_codes (uint8[nnz], host or device, nullable)
+ * receive the codes in CSR and CSC order when active.  Any pointer may be NULL.
+ */
+bm_status bm_get_codes(bm_handle h, int32_t* active, float* offset, uint8_t* csr_codes, uint8_t* csc_codes);
 
 /*
  * bm_set_factors -- set X = W H^T (caller orientation): W float[m*k],

@@ -145,6 +145,23 @@ def build_index(m: int, n: int, rows, cols, vals) -> Index:
                  r_s[csc2csr].astype(np.int32), a_s[csc2csr], csr2csc, csc2csr)
 
 
+def value_codes(ix: Index):
+    """One-byte encoding of the observed values (not part of the paper's
+    method; it only changes how A is stored): when every a_e is an integer
+    with |a_e| < 2^24 and max(a) - min(a) <= 255, a_e = code_e + offset with
+    offset = min(a) and code_e in [0, 255].  Returns (offset, CSR codes, CSC
+    codes) as uint8 arrays, or None when the values do not qualify."""
+    v = ix.val
+    if v.size == 0:
+        return None
+    if not np.all(v == np.rint(v)) or np.abs(v).max() >= 2.0 ** 24:
+        return None
+    lo, hi = float(v.min()), float(v.max())
+    if hi - lo > 255:
+        return None
+    return lo, (ix.val - lo).astype(np.uint8), (ix.cval - lo).astype(np.uint8)
+
+
 # ---------------------------------------------------------------------------
 # Loss and gradient of (MF) / (BM-nuclear)
 # ---------------------------------------------------------------------------

@@ -34,7 +34,8 @@ class bm_options(ctypes.Structure):
                 ("lmsvd_p", ctypes.c_int32), ("lmsvd_imax", ctypes.c_int32), ("lmsvd_min_iter", ctypes.c_int32),
                 ("lmsvd_tol", ctypes.c_double), ("tau", ctypes.c_double), ("ritz_rel", ctypes.c_double),
                 ("psi0", ctypes.c_double), ("k_init", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("autotune", ctypes.c_int32), ("step_rule", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("autotune", ctypes.c_int32), ("step_rule", ctypes.c_int32),
+                ("value_codec", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class bm_bb_options(ctypes.Structure):
@@ -92,6 +93,7 @@ _SIGS = {
     "bm_init": (_c.c_int, [_P, _c.POINTER(bm_prox_info)]),
     "bm_prox_step": (_c.c_int, [_P, _c.c_double, _c.POINTER(bm_prox_info)]),
     "bm_bb_default_options": (_c.c_int, [_c.POINTER(bm_bb_options)]),
+    "bm_get_codes": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_float), _P, _P]),
     "bm_set_bb_options": (_c.c_int, [_P, _c.POINTER(bm_bb_options)]),
     "bm_prox_step_bb": (_c.c_int, [_P, _c.POINTER(bm_prox_info), _c.POINTER(bm_bb_info)]),
     "bm_solve": (_c.c_int, [_P, _c.POINTER(bm_solve_opts), _c.POINTER(bm_solve_info)]),
@@ -244,6 +246,19 @@ def bm_prox_step(h, alpha=0.0):
     info = bm_prox_info()
     _check(lib().bm_prox_step(h, float(alpha), ctypes.byref(info)), h)
     return _info_dict(info)
+
+
+def bm_get_codes(h, nnz=None):
+    """(active, offset, csr_codes, csc_codes); the code arrays only when active and nnz is given."""
+    act = ctypes.c_int32()
+    off = ctypes.c_float()
+    _check(lib().bm_get_codes(h, ctypes.byref(act), ctypes.byref(off), None, None), h)
+    if not act.value or nnz is None:
+        return bool(act.value), off.value, None, None
+    a = np.zeros(nnz, np.uint8)
+    b = np.zeros(nnz, np.uint8)
+    _check(lib().bm_get_codes(h, None, None, _ptr(a), _ptr(b)), h)
+    return True, off.value, a, b
 
 
 def bm_bb_default_options() -> bm_bb_options:

@@ -285,6 +285,8 @@ bm_status bm_default_options(bm_options* o) {
   o->precision = 0;
   o->autotune = 0;
   o->step_rule = 0;
+  o->value_codec = 1;
+  o->pad_ = 0;
   o->seed = 0;
   return BM_OK;
 }
@@ -312,6 +314,7 @@ bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, cons
     BM_REQUIRE(o.lmsvd_p >= 0 && o.lmsvd_p <= 1, BM_ERR_INVALID, "bm_create: lmsvd_p must be 0 or 1");
     BM_REQUIRE(o.precision == 0 || o.precision == 1, BM_ERR_INVALID, "bm_create: precision must be 0 or 1");
     BM_REQUIRE(o.step_rule == 0 || o.step_rule == 1, BM_ERR_INVALID, "bm_create: step_rule must be 0 or 1");
+    BM_REQUIRE(o.value_codec == 0 || o.value_codec == 1, BM_ERR_INVALID, "bm_create: value_codec must be 0 or 1");
     BM_REQUIRE(o.lmsvd_imax >= 1 && o.k_init >= 1 && o.bm_epochs >= 0 && o.pg_steps >= 0, BM_ERR_INVALID,
                "bm_create: iteration counts out of range");
     h = new bm_ctx();
@@ -388,6 +391,22 @@ bm_status bm_dims(bm_handle h, int64_t* m, int64_t* n, int64_t* nnz, int32_t* tr
   if (transposed) *transposed = h->ix.transposed ? 1 : 0;
   if (k) *k = h->k;
   return BM_OK;
+}
+
+bm_status bm_get_codes(bm_handle h, int32_t* active, float* offset, uint8_t* csr_codes, uint8_t* csc_codes) {
+  if (!h) return BM_ERR_INVALID;
+  return guarded(h, [&] {
+    const Index& ix = h->ix;
+    if (active) *active = ix.codec ? 1 : 0;
+    if (offset) *offset = ix.code_off;
+    if (ix.codec && ix.nnz) {
+      if (csr_codes)
+        BM_CUDA(cudaMemcpyAsync(csr_codes, ix.val8.get(), ix.nnz, kind_to(csr_codes), h->stream));
+      if (csc_codes)
+        BM_CUDA(cudaMemcpyAsync(csc_codes, ix.cval8.get(), ix.nnz, kind_to(csc_codes), h->stream));
+    }
+    BM_CUDA(cudaStreamSynchronize(h->stream));
+  });
 }
 
 bm_status bm_get_index(bm_handle h, int64_t* row_ptr, int32_t* col, float* val, int64_t* col_ptr,

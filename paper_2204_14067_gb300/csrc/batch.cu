@@ -407,11 +407,13 @@ void build_tables(bm_batch_ctx& b) {
         a.ld_out = h.ld;
         if (pass == 0) {            // loss/gradient, CSR
           a.scal = ix.val.get(); a.o0 = h.W.get(); a.g0 = h.H.get(); a.g0b = h.Hb.get();
+          a.scal8 = ix.codec ? ix.val8.get() : nullptr; a.scal_off = ix.code_off;
           a.out = h.gW.get(); a.fseg = h.sc.fseg.get(); a.r_out = h.r_csr.get();
           ac.push_back(a);
           pc.push_back(pc.back() + sg.nseg);
         } else if (pass == 1) {     // loss/gradient, CSC
           a.scal = ix.cval.get(); a.o0 = h.H.get(); a.g0 = h.W.get(); a.g0b = h.Wb.get();
+          a.scal8 = ix.codec ? ix.cval8.get() : nullptr; a.scal_off = ix.code_off;
           a.out = h.gH.get();
           ah.push_back(a);
           ph.push_back(ph.back() + sg.nseg);

@@ -44,6 +44,12 @@ struct Index {
   DevBuf<int64_t> row_ptr, col_ptr;
   DevBuf<int32_t> col, row;       // CSR column ids, CSC row ids
   DevBuf<float> val, cval;        // A in CSR and in CSC order
+  // Value codec: when every observed value is an integer and they span at most
+  // 255, the loss/gradient passes read one byte per entry, a_e = code_e + code_off
+  // (exact in FP32 for |a| < 2^24); val / cval stay for the other uses.
+  bool codec = false;
+  float code_off = 0.f;
+  DevBuf<uint8_t> val8, cval8;
   DevBuf<int64_t> csr2csc;        // CSC position of CSR entry e
   DevBuf<int32_t> csc2csr;        // CSR position of CSC entry q (residual permutation)
   Segs rs, cs;                    // CSR (rows) and CSC (columns) work splits

@@ -132,6 +132,8 @@ void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
   a.nseg = sg.nseg;
   a.idx = csr ? ix.col.get() : ix.row.get();
   a.scal = csr ? ix.val.get() : ix.cval.get();
+  a.scal8 = ix.codec ? (csr ? ix.val8.get() : ix.cval8.get()) : nullptr;
+  a.scal_off = ix.code_off;
   a.o0 = csr ? h.W.get() : h.H.get();
   a.g0 = csr ? h.H.get() : h.W.get();
   a.ld = h.ld;

@@ -1,6 +1,7 @@
 // Index build for Omega: validation, CSR by (row, col), CSC by (col, row),
 // the CSR->CSC map and the segment work splits.  Sorting is an LSD radix sort
 // (8-bit digits, stable per pass) written for this library.
+#include <climits>
 #include <algorithm>
 
 #include "ctx.cuh"
@@ -401,6 +402,63 @@ int bits_for(uint64_t v) {  // number of bits to represent values < v
 
 }  // namespace
 
+// flags[0] = 1 if some value is not an integer; lo/hi = min/max as ordered int bits
+__global__ void k_codec_scan(const float* __restrict__ v, int64_t n, int* __restrict__ flags,
+                             int* __restrict__ lohi) {
+  int lo = INT_MAX, hi = INT_MIN, bad = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const float x = v[e];
+    if (!(x == rintf(x)) || fabsf(x) >= 16777216.f) {
+      bad = 1;
+    } else {
+      const int xi = (int)x;
+      lo = min(lo, xi);
+      hi = max(hi, xi);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(flags, 1);
+    atomicMin(lohi, lo);
+    atomicMax(lohi + 1, hi);
+  }
+}
+
+__global__ void k_codec_encode(const float* __restrict__ v, int64_t n, int off, uint8_t* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (uint8_t)((int)v[e] - off);
+}
+
+void build_codec(bm_ctx& h) {
+  Index& ix = h.ix;
+  cudaStream_t st = h.stream;
+  ix.codec = false;
+  if (ix.nnz == 0 || h.opt.value_codec == 0) return;
+  DevBuf<int> fl;
+  fl.alloc(4);
+  const int init[4] = {0, INT_MAX, INT_MIN, 0};
+  BM_CUDA(cudaMemcpyAsync(fl.get(), init, sizeof(init), cudaMemcpyHostToDevice, st));
+  k_codec_scan<<<grid_for(ix.nnz, 256), 256, 0, st>>>(ix.val.get(), ix.nnz, fl.get(), fl.get() + 1);
+  BM_CHECK_LAUNCH();
+  int hf[4];
+  BM_CUDA(cudaMemcpyAsync(hf, fl.get(), sizeof(hf), cudaMemcpyDeviceToHost, st));
+  BM_CUDA(cudaStreamSynchronize(st));
+  if (hf[0] || (int64_t)hf[2] - (int64_t)hf[1] > 255) return;
+  ix.val8.alloc(ix.nnz);
+  ix.cval8.alloc(ix.nnz);
+  k_codec_encode<<<grid_for(ix.nnz, 256), 256, 0, st>>>(ix.val.get(), ix.nnz, hf[1], ix.val8.get());
+  BM_CHECK_LAUNCH();
+  k_codec_encode<<<grid_for(ix.nnz, 256), 256, 0, st>>>(ix.cval.get(), ix.nnz, hf[1], ix.cval8.get());
+  BM_CHECK_LAUNCH();
+  BM_CUDA(cudaStreamSynchronize(st));
+  ix.code_off = (float)hf[1];
+  ix.codec = true;
+}
+
 void build_index(bm_ctx& h, int64_t m, int64_t n, int64_t nnz, const int32_t* rows_d,
                  const int32_t* cols_d, const float* vals_d) {
   cudaStream_t st = h.stream;
@@ -467,6 +525,7 @@ void build_index(bm_ctx& h, int64_t m, int64_t n, int64_t nnz, const int32_t* ro
   }
   build_segs(ix.rs, ix.row_ptr, ix.m, st);
   build_segs(ix.cs, ix.col_ptr, ix.n, st);
+  build_codec(h);
 }
 
 }  // namespace bm

@@ -56,7 +56,14 @@ struct PipeArgs {
   const void* g0b;        // BF16 copies of g0 / g1 (row stride ldb elements, ldb % 8 == 0,
   const void* g1b;        //   zero padded) used instead of g0 / g1 when gathering in BF16
   int ldb;
+  const uint8_t* scal8;   // MODE 0 value codec (nullable): A_e = scal8[e] + scal_off
+  float scal_off;
 };
+
+// the per-entry scalar of entry e: one byte through the value codec, else FP32
+__device__ __forceinline__ float load_scal(const PipeArgs& a, int64_t e) {
+  return a.scal8 ? (float)__ldg(a.scal8 + e) + a.scal_off : __ldg(a.scal + e);
+}
 
 __device__ __forceinline__ float bf16lo(unsigned u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf16hi(unsigned u) { return __uint_as_float(u & 0xffff0000u); }
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32) k_pipe(PipeArgs a) {
       const int64_t e = i_beg + (int64_t)BATCH * ib + lane;
       const bool v = e < i_end;
       j_pf = v ? __ldg(a.idx + e) : 0;
-      s_pf = v ? __ldg(a.scal + e) : 0.f;
+      s_pf = v ? load_scal(a, e) : 0.f;
     }
   };
   load_seg();
@@ -452,7 +459,7 @@ __device__ __forceinline__ void direct_segment(const PipeArgs& a, int64_t s) {
     const int64_t e = e0 + lane;
     const bool valid = e < end;
     const int j = valid ? __ldg(a.idx + e) : 0;
-    const float sv = valid ? __ldg(a.scal + e) : 0.f;
+    const float sv = valid ? load_scal(a, e) : 0.f;
 #pragma unroll 2
     for (int t = 0; t < kLanesPerEntry; ++t) {
       const int src = t * EPS + g;
