@@ -11,7 +11,8 @@ second per cycle (nnz / cycle time) summed over replicas.
 `--mode tto` times a solve to the FP64 oracle's objective on the planted
 500 x 300 problem; `--mode serve` measures the continuous-batching server.
 `--mode edm` times the distance-geometry loss/gradient and `--mode edm_solve`
-the cycles of Algorithm 1 on the distance-geometry QSDP (30,000-point chain).
+the cycles of Algorithm 1 on the distance-geometry QSDP (30,000-point chain);
+`--mode bcd` compares the column-block BM solver with the PR+ BM phase.
 `--impl reference` times the FP64 oracle on the host cores on a bounded
 sample of the same workload.
 """
@@ -749,6 +750,55 @@ def run_edm_solve(args):
     }
 
 
+def run_bcd(args):
+    """Column-block coordinate descent (the polyMF-SS form of the BM phase)
+    against the full-gradient PR+ BM phase on the netflix-shaped workload, k =
+    64, from the same factors: time per epoch (one sweep over the k column
+    blocks, resp. one PR+ iteration) and the objective after each epoch."""
+    import torch
+
+    import paper_2204_14067_gb300 as B
+    from synth import named_config, random_factors
+
+    p = named_config(args.config)
+    k = min(K_BENCH, p.k_max)
+    W0, H0 = random_factors(p.m, p.n, k, seed=11, scale=0.1)
+    out = {}
+    for solver in ("pr_cg", "column_blocks"):
+        opt = B.bm_default_options()
+        opt.value_codec = args.codec
+        h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, p.k_max, opt)
+        stream = torch.cuda.Stream()
+        B.bm_set_stream(h, stream)
+        B.bm_set_factors(h, k, W0, H0)
+        step = (lambda: B.bm_bcd_phase(h, 1)) if solver == "column_blocks" else (lambda: B.bm_bm_phase(h, 1))
+        F = [B.bm_loss_grad(h)[1]]
+        for _ in range(args.warmup):
+            F.append(step())
+        B.bm_profile_enable(h, True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            F.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        prof = B.bm_profile_read(h)
+        B.bm_profile_enable(h, False)
+        B.bm_destroy(h)
+        out[solver] = {"ms_per_epoch": ev0.elapsed_time(ev1) / args.steps, "F": F,
+                       "kernels": {kk: {"launches": v[0], "ms": round(v[1], 3)} for kk, v in sorted(prof.items())}}
+    ms = out["column_blocks"]["ms_per_epoch"]
+    return {
+        "metric": "column-block BM sweep nnz/s", "value": p.nnz / (ms / 1e3), "unit": "nnz/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.config}-shaped, nnz={p.nnz}, k={k}, lambda={p.lam}",
+                   "step": "one sweep over the k column blocks (column_blocks) / one PR+ iteration (pr_cg)"},
+        "column_blocks": out["column_blocks"], "pr_cg": out["pr_cg"],
+    }
+
+
 def _dist_cpu():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return None, int(os.environ.get("RANK", "0")), ws
@@ -760,7 +810,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="cycle", choices=["cycle", "grad", "tto", "serve", "edm", "edm_solve"])
+    ap.add_argument("--mode", default="cycle", choices=["cycle", "grad", "tto", "serve", "edm", "edm_solve", "bcd"])
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="1: BF16 copies of the gathered factor rows (cycle and grad modes)")
     ap.add_argument("--serve-count", type=int, default=24)
@@ -784,6 +834,8 @@ def main():
         line = run_edm(args)
     elif args.mode == "edm_solve":
         line = run_edm_solve(args)
+    elif args.mode == "bcd":
+        line = run_bcd(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -71,7 +71,9 @@ typedef struct {
   int32_t value_codec;   /* 1: when every observed value is an integer and they span at most
                             255, the loss/gradient passes read one byte per entry
                             (a = code + offset, exact); 0: always FP32 values; 1 */
-  int32_t pad_;
+  int32_t bm_solver;     /* BM phase of bm_solve: 0 Polak-Ribiere+ CG on all of (W, H) with
+                            the exact line search; 1 column-block coordinate descent
+                            (bm_bcd_phase); 0 */
 } bm_options;
 
 /* Result of one inexact PG step (Eq. "inexactpg", "truncate"). */
@@ -443,6 +445,18 @@ bm_status bm_loss_grad_csr_noalloc(int64_t m, int64_t n, const int64_t* row_ptr,
                                    const float* val, const float* W, const float* H, int32_t k, int32_t ld,
                                    double lambda, float* gW, double* f, void* stream);
 const char* bm_noalloc_last_error(void);
+
+/*
+ * bm_bcd_phase -- `epochs` sweeps of column-block coordinate descent on (MF):
+ * the form of polyMF-SS the paper adopts for the BM phase of matrix
+ * completion (matrix completion experiments: each block is one column of W
+ * and the same column of H, exact line search).  Block c: g_w = R h_c +
+ * lambda w_c, g_h = R^T w_c + lambda h_c, direction -(g_w, g_h), step = the
+ * minimiser over s >= 0 of the objective's quartic along it (the rule of
+ * bm_bm_phase); columns in order 0..k-1.  *F (nullable) = F after the last
+ * block.  Errors: BM_ERR_INVALID for epochs < 0; BM_ERR_NUMERIC.
+ */
+bm_status bm_bcd_phase(bm_handle h, int32_t epochs, double* F);
 
 /*
  * The SpaRSA step rule for the PG step (supplement Sec. "The SpaRSA variant

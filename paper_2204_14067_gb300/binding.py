@@ -35,7 +35,7 @@ class bm_options(ctypes.Structure):
                 ("lmsvd_tol", ctypes.c_double), ("tau", ctypes.c_double), ("ritz_rel", ctypes.c_double),
                 ("psi0", ctypes.c_double), ("k_init", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("autotune", ctypes.c_int32), ("step_rule", ctypes.c_int32),
-                ("value_codec", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("value_codec", ctypes.c_int32), ("bm_solver", ctypes.c_int32)]
 
 
 class bm_bb_options(ctypes.Structure):
@@ -93,6 +93,7 @@ _SIGS = {
     "bm_init": (_c.c_int, [_P, _c.POINTER(bm_prox_info)]),
     "bm_prox_step": (_c.c_int, [_P, _c.c_double, _c.POINTER(bm_prox_info)]),
     "bm_bb_default_options": (_c.c_int, [_c.POINTER(bm_bb_options)]),
+    "bm_bcd_phase": (_c.c_int, [_P, _c.c_int32, _c.POINTER(_c.c_double)]),
     "bm_get_codes": (_c.c_int, [_P, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_float), _P, _P]),
     "bm_set_bb_options": (_c.c_int, [_P, _c.POINTER(bm_bb_options)]),
     "bm_prox_step_bb": (_c.c_int, [_P, _c.POINTER(bm_prox_info), _c.POINTER(bm_bb_info)]),
@@ -246,6 +247,13 @@ def bm_prox_step(h, alpha=0.0):
     info = bm_prox_info()
     _check(lib().bm_prox_step(h, float(alpha), ctypes.byref(info)), h)
     return _info_dict(info)
+
+
+def bm_bcd_phase(h, epochs):
+    """`epochs` sweeps of the column-block BM solver; returns F after them."""
+    F = ctypes.c_double()
+    _check(lib().bm_bcd_phase(h, int(epochs), ctypes.byref(F)), h)
+    return F.value
 
 
 def bm_get_codes(h, nnz=None):

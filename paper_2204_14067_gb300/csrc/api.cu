@@ -286,7 +286,7 @@ bm_status bm_default_options(bm_options* o) {
   o->autotune = 0;
   o->step_rule = 0;
   o->value_codec = 1;
-  o->pad_ = 0;
+  o->bm_solver = 0;
   o->seed = 0;
   return BM_OK;
 }
@@ -315,6 +315,7 @@ bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, cons
     BM_REQUIRE(o.precision == 0 || o.precision == 1, BM_ERR_INVALID, "bm_create: precision must be 0 or 1");
     BM_REQUIRE(o.step_rule == 0 || o.step_rule == 1, BM_ERR_INVALID, "bm_create: step_rule must be 0 or 1");
     BM_REQUIRE(o.value_codec == 0 || o.value_codec == 1, BM_ERR_INVALID, "bm_create: value_codec must be 0 or 1");
+    BM_REQUIRE(o.bm_solver == 0 || o.bm_solver == 1, BM_ERR_INVALID, "bm_create: bm_solver must be 0 or 1");
     BM_REQUIRE(o.lmsvd_imax >= 1 && o.k_init >= 1 && o.bm_epochs >= 0 && o.pg_steps >= 0, BM_ERR_INVALID,
                "bm_create: iteration counts out of range");
     h = new bm_ctx();
@@ -368,6 +369,8 @@ void bm_destroy(bm_handle h) {
   prox_destroy(*h);
   bb_destroy(h->bb);
   h->bb = nullptr;
+  bcd_destroy(h->bcd);
+  h->bcd = nullptr;
   cudaStream_t own = h->own_stream;
   delete h;
   if (own) cudaStreamDestroy(own);
@@ -601,7 +604,8 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
     int outer = 0;
     for (outer = 1; outer <= so.max_outer; ++outer) {
       double F_bm = 0.0;
-      F = bm_phase_dev(*h, h->opt.bm_epochs, &F_bm);
+      F = h->opt.bm_solver == 1 ? bcd_phase_dev(*h, h->opt.bm_epochs, &F_bm)
+                                : bm_phase_dev(*h, h->opt.bm_epochs, &F_bm);
       BM_REQUIRE(std::isfinite(F), BM_ERR_NUMERIC, "bm_solve: objective is not finite");
       if (have_prev) {
         if (so.F_target > 0 && F <= so.F_target) { converged = true; break; }

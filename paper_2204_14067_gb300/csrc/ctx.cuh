@@ -88,6 +88,7 @@ struct Scratch {
 
 struct ProxState;  // defined in prox.cu
 struct BbState;    // defined in sparsa.cu (SpaRSA step rule)
+struct BcdState;   // defined in bcd.cu (column-block BM solver)
 
 // Optional per-kernel event timing (bm_profile_enable).
 struct Profiler {
@@ -123,6 +124,7 @@ struct bm_ctx {
   bm::Scratch sc;
   bm::ProxState* ps = nullptr;
   bm::BbState* bb = nullptr;     // SpaRSA step-rule state (created on first use)
+  bm::BcdState* bcd = nullptr;   // column-block BM solver scratch (created on first use)
   bm::Profiler prof;
   std::string err;
   bool bm_changed = false;       // BM phase moved since the last PG step
@@ -222,6 +224,10 @@ void prox_step_dev(bm_ctx& h, double alpha, bm_prox_info* info, bool eval_F = tr
 void prox_step_bb_dev(bm_ctx& h, bm_prox_info* info, bm_bb_info* bb);
 void bb_reset(bm_ctx& h);
 void bb_destroy(BbState* s);
+// `epochs` sweeps of the column-block BM solver (bcd.cu); returns F at entry,
+// *F_out = F after the sweeps.
+double bcd_phase_dev(bm_ctx& h, int epochs, double* F_out);
+void bcd_destroy(BcdState* s);
 void init_step_dev(bm_ctx& h, bm_prox_info* info);
 // Checkpoint of the PG-step state (warm start and safeguard): size, save
 // into host memory, load from host memory (validated; BM_ERR_INVALID).
