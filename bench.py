@@ -179,6 +179,8 @@ def run_ours(args):
     opt = B.bm_default_options()
     opt.precision = args.precision
     opt.value_codec = args.codec
+    if args.lmsvd_tol is not None:
+        opt.lmsvd_tol = args.lmsvd_tol
     h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, p.k_max, opt)
     codec_on = B.bm_get_codes(h)[0]
     stream = torch.cuda.Stream()
@@ -440,6 +442,8 @@ def run_tto(args):
     target = F_star * (1 + 1e-6)
     opts = B.bm_default_options()
     opts.step_rule = args.step_rule
+    if args.lmsvd_tol is not None:
+        opts.lmsvd_tol = args.lmsvd_tol
     runs = []
     for rep in range(args.warmup + args.steps):
         torch.cuda.synchronize()
@@ -837,6 +841,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="1: BF16 copies of the gathered factor rows (cycle and grad modes)")
     ap.add_argument("--serve-count", type=int, default=24)
+    ap.add_argument("--lmsvd-tol", type=float, default=None,
+                    help="LmSVD stop tolerance (cycle and tto modes; default: the library's)")
     ap.add_argument("--codec", type=int, default=1, choices=[0, 1],
                     help="1: one-byte codes for integer observed values in the loss/gradient passes")
     ap.add_argument("--step-rule", type=int, default=0, choices=[0, 1],

@@ -58,7 +58,9 @@ typedef struct {
   int32_t lmsvd_p;       /* LmSVD memory p_t (Algorithm 2); 1 */
   int32_t lmsvd_imax;    /* LmSVD iteration cap; 50 */
   int32_t lmsvd_min_iter;/* Rayleigh-Ritz steps before the stop test; 2 */
-  double lmsvd_tol;      /* stop when max |theta - theta_prev| <= tol * theta_1; 1e-6 */
+  double lmsvd_tol;      /* stop when max |theta - theta_prev| <= tol * theta_1; 1e-5 (FP32
+                            resolves the Ritz values to about eps32 * theta_1; a tighter test
+                            spends iterations on rounding) */
   double tau;            /* orth(): drop Gram eigenvalues <= tau (Eq. "orth-W"); 1e-6 */
   double ritz_rel;       /* Algorithm 2 J_s: keep s_j > ritz_rel * s_1; 1e-6 */
   double psi0;           /* safeguard noise level psi_0 (Sec. "Ensuring sufficient precision"); 0.1 */

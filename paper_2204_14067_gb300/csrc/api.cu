@@ -277,7 +277,7 @@ bm_status bm_default_options(bm_options* o) {
   o->lmsvd_p = 1;
   o->lmsvd_imax = 50;
   o->lmsvd_min_iter = 2;
-  o->lmsvd_tol = 1e-6;
+  o->lmsvd_tol = 1e-5;
   o->tau = 1e-6;
   o->ritz_rel = 1e-6;
   o->psi0 = 0.1;
