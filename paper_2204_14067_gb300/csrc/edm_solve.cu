@@ -21,6 +21,7 @@
 
 #include "dense.cuh"
 #include "edm.cuh"
+#include "quartic.cuh"
 
 namespace bm {
 
@@ -34,6 +35,15 @@ struct EdmSolveState {
   DevBuf<double> G, E, ev, colsum;
   DevBuf<double> rowbuf, segsums, sums4;   // per-row bounds, line-search partials
   DevBuf<double> dotpart, scal;            // dot-product partials; 8 scalars read back per sync
+  DevBuf<double> ctl;                      // BM-phase control scalars (device-resident)
+  // the BM phase's iterations as one CUDA graph, re-captured when the row
+  // stride, the iteration count or the stream changes
+  cudaGraphExec_t bm_graph = nullptr;
+  int graph_ld = -1, graph_epochs = -1;
+  cudaStream_t graph_stream = nullptr;
+  ~EdmSolveState() {
+    if (bm_graph) cudaGraphExecDestroy(bm_graph);
+  }
   DevBuf<float> Ts;
   double alpha = 0, sigma = 0;
   int ku = 0;              // columns of U_t in blk[kUp]
@@ -307,6 +317,77 @@ __global__ void __launch_bounds__(kSumThreads) k_dots2_final(const double* __res
     __syncthreads();
   }
   if (threadIdx.x < 2) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// BM-phase control scalars, kept on the device (slots of EdmSolveState::ctl)
+enum { kCF = 0, kCBeta, kCGGPrev, kCFirst, kCStep, kCFLast, kCGG, kCGP, kCDoG, kCGD, kCDD, kCS1, kCS2, kCS3,
+       kCS4, kCBad, kCtlSlots };
+
+__global__ void k_edm_ctrl_init(double* __restrict__ ctl) {
+  for (int i = threadIdx.x; i < kCtlSlots; i += blockDim.x) ctl[i] = i == kCFirst ? 1.0 : 0.0;
+}
+
+// F of the current factor, and beta of Polak-Ribiere+ with the restart rule:
+// beta = 0 when <-g + beta D_prev, g> >= 0 (not a descent direction)
+__global__ void k_edm_ctrl_dir(double* __restrict__ ctl, const double* __restrict__ F) {
+  const double f = F[0], gg = ctl[kCGG], gp = ctl[kCGP], dog = ctl[kCDoG];
+  double beta = 0.0;
+  if (ctl[kCFirst] == 0.0 && ctl[kCGGPrev] > 0) {
+    beta = fmax(0.0, (gg - gp) / ctl[kCGGPrev]);
+    if (beta > 0 && -gg + beta * dog >= 0) beta = 0.0;
+  }
+  if (!isfinite(f)) ctl[kCBad] = 1.0;
+  ctl[kCF] = f;
+  ctl[kCBeta] = beta;
+  ctl[kCGGPrev] = gg;
+  ctl[kCFirst] = 0.0;
+}
+
+// step = argmin over s >= 0 of g(V + s D) (each pair twice among the directed entries)
+__global__ void k_edm_ctrl_step(double* __restrict__ ctl, double lam) {
+  double c[5];
+  c[0] = ctl[kCF];
+  c[1] = ctl[kCGD];
+  c[2] = 0.25 * ctl[kCS2] + lam * ctl[kCDD];
+  c[3] = 0.5 * ctl[kCS3];
+  c[4] = 0.25 * ctl[kCS4];
+  const double st = quartic_argmin_d(c);
+  ctl[kCStep] = st;
+  ctl[kCFLast] = st > 0 ? poly4d(c, st) : c[0];
+  if (!isfinite(ctl[kCFLast])) ctl[kCBad] = 1.0;
+}
+
+// D = -g + beta D (D not read when beta = 0: it may hold no direction yet)
+__global__ void k_edm_dir(float4* __restrict__ D, const float4* __restrict__ g, int64_t n4,
+                          const double* __restrict__ ctl) {
+  const float beta = (float)ctl[kCBeta];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 gv = g[i];
+    float4 v = beta != 0.f ? D[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    v.x = fmaf(beta, v.x, -gv.x);
+    v.y = fmaf(beta, v.y, -gv.y);
+    v.z = fmaf(beta, v.z, -gv.z);
+    v.w = fmaf(beta, v.w, -gv.w);
+    D[i] = v;
+  }
+}
+
+// V += step D; g_prev = g
+__global__ void k_edm_update(float4* __restrict__ V, const float4* __restrict__ D, const float4* __restrict__ g,
+                             float4* __restrict__ gp, int64_t n4, const double* __restrict__ ctl) {
+  const float st = (float)ctl[kCStep];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    if (st > 0.f) {
+      const float4 d = D[i];
+      float4 x = V[i];
+      x.x = fmaf(st, d.x, x.x);
+      x.y = fmaf(st, d.y, x.y);
+      x.z = fmaf(st, d.z, x.z);
+      x.w = fmaf(st, d.w, x.w);
+      V[i] = x;
+    }
+    gp[i] = g[i];
+  }
 }
 
 // coef_e = alpha w_e r_e (r_e of the directed entry; r_e = -d_e^2 when V = 0)
@@ -657,6 +738,7 @@ void ensure_state(bm_edm_ctx& h) {
   s->sums4.alloc(4 * (sum_parts() + 1));
   s->dotpart.alloc(2 * (size_t)sum_parts());
   s->scal.alloc(8);
+  s->ctl.alloc(32);
   // SpMM partial rows up to 128 columns
   const int64_t need = std::max<int64_t>(1, h.seg.nslots) * 128;
   if ((int64_t)h.partial.n < need) {
@@ -763,30 +845,41 @@ void dots2(bm_edm_ctx& h, const float* x0, const float* y0, const float* x1, con
 }
 
 // Polak-Ribiere+ with the exact quartic line search; returns F after the last iteration
-double bm_phase(bm_edm_ctx& h, int epochs) {
+// Launch the BM phase's `epochs` iterations: every decision (beta, restart,
+// step) is taken on the device, so they run back to back without host round
+// trips (and can be captured as one graph).
+void bm_phase_launch(bm_edm_ctx& h, int epochs) {
   EdmSolveState& s = *h.ss;
   bm_ctx& cx = core(h);
-  if (h.k == 0 || epochs <= 0) return edm_loss_grad_dev(h, false, nullptr);
-  const int64_t cnt = h.n * (int64_t)h.ld;
-  double* sc = s.scal.get();
-  // quartic coefficients of g(V + s D): the line-search sums (each pair appears
-  // twice among the directed entries) and <g, D>, <D, D>, read back in one sync
-  auto quartic = [&](double F, double c[5]) {
-    PairArgs a{};
-    a.seg_row = h.seg.row.get();
-    a.seg_beg = h.seg.beg.get();
-    a.seg_end = h.seg.end.get();
-    a.seg_slot = h.seg.slot.get();
-    a.nseg = h.seg.nseg;
-    a.col = h.col.get();
-    a.U = h.V.get();
-    a.D = s.D.get();
-    a.dsq = h.dsq.get();
-    a.w = h.w.get();
-    a.ld = h.ld;
-    a.nchunk = h.ld / 4;
-    a.sums = s.segsums.get();
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(a.nseg, 8), (int64_t)num_sms() * 16));
+  const int64_t cnt = h.n * (int64_t)h.ld, n4 = cnt / 4;
+  double* ctl = s.ctl.get();
+  BM_LAUNCH(cx, "edm_ctrl", k_edm_ctrl_init<<<1, 32, 0, h.stream>>>(ctl));
+  PairArgs a{};
+  a.seg_row = h.seg.row.get();
+  a.seg_beg = h.seg.beg.get();
+  a.seg_end = h.seg.end.get();
+  a.seg_slot = h.seg.slot.get();
+  a.nseg = h.seg.nseg;
+  a.col = h.col.get();
+  a.U = h.V.get();
+  a.D = s.D.get();
+  a.dsq = h.dsq.get();
+  a.w = h.w.get();
+  a.ld = h.ld;
+  a.nchunk = h.ld / 4;
+  a.sums = s.segsums.get();
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(a.nseg, 8), (int64_t)num_sms() * 16));
+  const int parts = sum_parts();
+  float4* V4 = reinterpret_cast<float4*>(h.V.get());
+  float4* D4 = reinterpret_cast<float4*>(s.D.get());
+  float4* g4 = reinterpret_cast<float4*>(h.gV.get());
+  float4* gp4 = reinterpret_cast<float4*>(s.gp.get());
+  for (int e = 0; e < epochs; ++e) {
+    edm_loss_grad_dev(h, true, nullptr, false);                      // g(V) into h.red[0], gradient
+    dots2(h, h.gV.get(), h.gV.get(), h.gV.get(), e > 0 ? s.gp.get() : h.gV.get(), ctl + kCGG);
+    if (e > 0) dots2(h, s.D.get(), h.gV.get(), s.D.get(), s.D.get(), ctl + kCDoG);
+    BM_LAUNCH(cx, "edm_ctrl", k_edm_ctrl_dir<<<1, 1, 0, h.stream>>>(ctl, h.red.get()));
+    BM_LAUNCH(cx, "edm_dir", k_edm_dir<<<grid_n(n4), 256, 0, h.stream>>>(D4, g4, n4, ctl));
     switch ((a.nchunk + 3) / 4) {
       case 1: BM_LAUNCH(cx, "edm_ls", k_pair_ls<1><<<grid, 256, 0, h.stream>>>(a)); break;
       case 2: BM_LAUNCH(cx, "edm_ls", k_pair_ls<2><<<grid, 256, 0, h.stream>>>(a)); break;
@@ -798,52 +891,59 @@ double bm_phase(bm_edm_ctx& h, int epochs) {
       default: BM_LAUNCH(cx, "edm_ls", k_pair_ls<8><<<grid, 256, 0, h.stream>>>(a)); break;
     }
     // block partials, then one pass of the same kernel over them (fixed order)
-    const int parts = sum_parts();
     BM_LAUNCH(cx, "edm_sum4", k_sum4_part<<<parts, kSumThreads, 0, h.stream>>>(s.segsums.get(), a.nseg,
                                                                                  s.sums4.get() + 4));
-    BM_LAUNCH(cx, "edm_sum4", k_sum4_part<<<1, kSumThreads, 0, h.stream>>>(s.sums4.get() + 4, parts, sc + 4));
-    dots2(h, h.gV.get(), s.D.get(), s.D.get(), s.D.get(), sc + 2);
-    std::vector<double> v = d2h(h, sc + 2, 6);   // <g, D>, <D, D>, S1..S4
-    c[0] = F;
-    c[1] = v[0];                                 // <grad g, D>
-    c[2] = 0.25 * v[3] + h.lambda * v[1];
-    c[3] = 0.5 * v[4];
-    c[4] = 0.25 * v[5];
-  };
-  double F = 0.0, gg_prev = 0.0;
-  bool have_prev = false;
-  for (int e = 0; e < epochs; ++e) {
-    edm_loss_grad_dev(h, true, nullptr, false);
-    dots2(h, h.gV.get(), h.gV.get(), h.gV.get(), have_prev ? s.gp.get() : h.gV.get(), sc);
-    double head[3];
-    BM_CUDA(cudaMemcpyAsync(head, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h.stream));
-    BM_CUDA(cudaMemcpyAsync(head + 2, h.red.get(), sizeof(double), cudaMemcpyDeviceToHost, h.stream));
-    BM_CUDA(cudaStreamSynchronize(h.stream));
-    F = head[2];
-    BM_REQUIRE(std::isfinite(F), BM_ERR_NUMERIC, "distance-geometry loss is not finite");
-    const double gg = head[0];
-    double beta = 0.0;
-    if (have_prev && gg_prev > 0) beta = std::max(0.0, (gg - head[1]) / gg_prev);
-    if (!have_prev) BM_CUDA(cudaMemsetAsync(s.D.get(), 0, cnt * sizeof(float), h.stream));
-    xpby_dev(cx, s.D.get(), h.gV.get(), (float)beta, cnt);   // D = -g + beta D
-    double c[5];
-    quartic(F, c);
-    if (beta > 0 && c[1] >= 0) {   // not a descent direction: restart with D = -g
-      xpby_dev(cx, s.D.get(), h.gV.get(), 0.f, cnt);
-      quartic(F, c);
-    }
-    const double st = quartic_argmin_ext(c);
-    if (st > 0) {
-      axpy_dev(cx, h.V.get(), s.D.get(), (float)st, cnt);
-      F = (((c[4] * st + c[3]) * st + c[2]) * st + c[1]) * st + c[0];
-    }
-    if (e + 1 < epochs)
-      BM_CUDA(cudaMemcpyAsync(s.gp.get(), h.gV.get(), cnt * sizeof(float), cudaMemcpyDeviceToDevice, h.stream));
-    gg_prev = gg;
-    have_prev = true;
+    BM_LAUNCH(cx, "edm_sum4", k_sum4_part<<<1, kSumThreads, 0, h.stream>>>(s.sums4.get() + 4, parts, ctl + kCS1));
+    dots2(h, h.gV.get(), s.D.get(), s.D.get(), s.D.get(), ctl + kCGD);   // <g, D>, <D, D>
+    BM_LAUNCH(cx, "edm_ctrl", k_edm_ctrl_step<<<1, 1, 0, h.stream>>>(ctl, h.lambda));
+    BM_LAUNCH(cx, "edm_update", k_edm_update<<<grid_n(n4), 256, 0, h.stream>>>(V4, D4, g4, gp4, n4, ctl));
   }
+}
+
+// Polak-Ribiere+ with the exact quartic line search; returns F after the last iteration
+double bm_phase(bm_edm_ctx& h, int epochs) {
+  EdmSolveState& s = *h.ss;
+  if (h.k == 0 || epochs <= 0) return edm_loss_grad_dev(h, false, nullptr);
+  bool launched = false;
+  if (!core(h).prof.on) {   // timed runs record events around each launch: no graph then
+    if (s.bm_graph && (s.graph_ld != h.ld || s.graph_epochs != epochs || s.graph_stream != h.stream)) {
+      cudaGraphExecDestroy(s.bm_graph);
+      s.bm_graph = nullptr;
+    }
+    if (!s.bm_graph) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        bool ok = true;
+        try {
+          bm_phase_launch(h, epochs);
+        } catch (...) {
+          ok = false;
+        }
+        const cudaError_t ce = cudaStreamEndCapture(h.stream, &g);
+        ok = ok && ce == cudaSuccess && g;
+        if (ok && cudaGraphInstantiate(&s.bm_graph, g, 0) == cudaSuccess) {
+          s.graph_ld = h.ld;
+          s.graph_epochs = epochs;
+          s.graph_stream = h.stream;
+        } else {
+          s.bm_graph = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+      }
+      cudaGetLastError();   // a failed capture falls back to direct launches
+    }
+    if (s.bm_graph) {
+      BM_CUDA(cudaGraphLaunch(s.bm_graph, h.stream));
+      launched = true;
+    }
+  }
+  if (!launched) bm_phase_launch(h, epochs);
+  double out[kCtlSlots];
+  BM_CUDA(cudaMemcpyAsync(out, s.ctl.get(), sizeof(out), cudaMemcpyDeviceToHost, h.stream));
   BM_CUDA(cudaStreamSynchronize(h.stream));
-  return F;
+  BM_REQUIRE(out[kCBad] == 0.0 && std::isfinite(out[kCFLast]), BM_ERR_NUMERIC,
+             "distance-geometry BM phase: objective is not finite");
+  return out[kCFLast];
 }
 
 template <class Fn>
