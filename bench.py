@@ -89,22 +89,31 @@ def _dist():
     return None, 0, 1
 
 
-def _maxall(dist, x):
+def _reduce(dist, x, op):
+    """All-reduce one host scalar over the replicas (NCCL on GPUs, gloo on CPU)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _maxall(dist, x):
+    return x if dist is None else _reduce(dist, x, dist.ReduceOp.MAX)
 
 
 def _sumall(dist, x):
-    if dist is None:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return x if dist is None else _reduce(dist, x, dist.ReduceOp.SUM)
+
+
+def replica_throughput(dist, ms_per_step, units_per_step):
+    """Whole-job figures of N independent replicas: the slowest rank's step
+    time and the units all ranks processed per step over it."""
+    ms = _maxall(dist, ms_per_step)
+    units = _sumall(dist, float(units_per_step))
+    return ms, units, units / (ms / 1e3)
 
 
 def algorithmic_bytes(kernel, d, k, q, vb=4):
@@ -258,9 +267,7 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     B.bm_destroy(h)
 
-    ms_step = _maxall(dist, ms / args.steps)
-    total_units = _sumall(dist, float(p.nnz))
-    value = total_units / (ms_step / 1e3)
+    ms_step, total_units, value = replica_throughput(dist, ms / args.steps, p.nnz)
     e2e_val = _sumall(dist, float(p.nnz)) / _maxall(dist, e2e_s)
     if rank != 0:
         return None
