@@ -826,16 +826,17 @@ def run_bcd(args):
         out[solver] = {"ms_per_epoch": ev0.elapsed_time(ev1) / args.steps, "F": F,
                        "kernels": {kk: {"launches": v[0], "ms": round(v[1], 3)} for kk, v in sorted(prof.items())}}
     ms = out["column_blocks"]["ms_per_epoch"]
-    # dominant kernel: the residual update, 12 B per entry (index, residual read
-    # and write); the four column vectors it reads are L2-resident
-    kb = out["column_blocks"]["kernels"].get("bcd_update")
+    # dominant kernel: the residual update fused with the next block's gradient,
+    # 12 B per entry (index, residual read and write); the six column vectors it
+    # reads are L2-resident
+    kb = out["column_blocks"]["kernels"].get("bcd_update_spmv")
     roof = None
     if kb:
         peaks, kind = _load_peaks()
         by = p.nnz * 12
         avg = kb["ms"] / max(1, kb["launches"])
         ach = by / (avg / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "bcd_update", "achieved": ach, "peak": float(peaks["hbm_gbs"]),
+        roof = {"bound": "hbm", "kernel": "bcd_update_spmv", "achieved": ach, "peak": float(peaks["hbm_gbs"]),
                 "unit": "GB/s", "frac": ach / float(peaks["hbm_gbs"]), "traffic": None, "peak_source": kind,
                 "bytes_per_launch": by, "avg_launch_ms": avg}
     return {

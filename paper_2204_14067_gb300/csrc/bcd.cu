@@ -11,7 +11,9 @@
 //   minimised over s >= 0 (the full-gradient BM phase's rule); then w_c, h_c
 //   and the residual (CSR and CSC order) are updated in place.
 //
-// Every pass is a warp per row (column) segment of the existing work splits;
+// Every pass is a warp per row (column) segment of the existing work splits,
+// and block c's residual update shares its two passes with block c+1's
+// gradient (three passes over Omega per block);
 // the column being updated is copied to contiguous vectors first so the
 // per-entry gathers read 4 bytes from an L2-resident vector.  Rows spanning
 // several segments use the partial slots and a fixed-order fix-up, and the
@@ -27,6 +29,7 @@ namespace bm {
 
 struct BcdState {
   DevBuf<float> wc, hc, gw, gh;     // column c of W and H, block gradients (contiguous)
+  DevBuf<float> wn, hn, gwn, ghn;   // the same for column c+1 (the fused passes fill them)
   DevBuf<double> segs4;             // line-search sums per CSR segment (4 each)
   DevBuf<double> part, out;         // reduction partials and the 5 scalars read back
 };
@@ -62,29 +65,6 @@ __global__ void k_col_get(const float* __restrict__ X, int ld, int c, int64_t ro
 __global__ void k_col_axpy(float* __restrict__ X, int ld, int c, int64_t rows, const float* __restrict__ d, float s) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
     X[i * ld + c] = fmaf(s, d[i], X[i * ld + c]);
-}
-
-// out_i = sum_{e in row i} r_e x[idx_e] + lam own_i (rows over several segments: partials)
-__global__ void __launch_bounds__(kThreads) k_col_spmv(SegView sg, const int32_t* __restrict__ idx,
-                                                      const float* __restrict__ r, const float* __restrict__ x,
-                                                      const float* __restrict__ own, float lam,
-                                                      float* __restrict__ out, float* __restrict__ partial) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < sg.nseg; s += nwarps) {
-    const int64_t beg = sg.beg[s], end = sg.end[s];
-    float acc = 0.f;
-    for (int64_t e = beg + lane; e < end; e += 32) acc = fmaf(__ldg(r + e), __ldg(x + __ldg(idx + e)), acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (lane == 0) {
-      const int slot = sg.slot[s];
-      const int i = sg.row[s];
-      if (slot < 0)
-        out[i] = fmaf(lam, own[i], acc);
-      else
-        partial[slot] = acc;
-    }
-  }
 }
 
 __global__ void k_col_fixup(const int32_t* __restrict__ mrow, const int32_t* __restrict__ mfirst,
@@ -155,6 +135,51 @@ __global__ void __launch_bounds__(kThreads) k_col_update(SegView sg, const int32
   }
 }
 
+// The residual update of block c fused with the block gradient of block c+1
+// over the same segments: r_e += step b_e + step^2 cc_e (block c's vectors;
+// skipped when update is false), then out_o = sum_e r_e x[idx_e] + lam own_o
+// (block c+1's vectors), with the partial slots of the plain column SpMV.
+// The arithmetic per entry is that of k_col_update followed by a plain column SpMV.
+struct FusedCols {
+  const float *wc, *hc, *gw, *gh;   // block c (update)
+  float step;
+  bool update;
+  const float *x, *own;             // block c+1: gathered vector and owned vector
+};
+__global__ void __launch_bounds__(kThreads) k_col_update_spmv(SegView sg, const int32_t* __restrict__ idx,
+                                                             bool own_is_row, float* __restrict__ r, FusedCols f,
+                                                             float lam, float* __restrict__ out,
+                                                             float* __restrict__ partial) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float s2 = f.step * f.step;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < sg.nseg; s += nwarps) {
+    const int o = sg.row[s];
+    const int64_t beg = sg.beg[s], end = sg.end[s];
+    float acc = 0.f;
+    for (int64_t e = beg + lane; e < end; e += 32) {
+      const int xi = __ldg(idx + e);
+      float re = r[e];
+      if (f.update) {
+        const int i = own_is_row ? o : xi, j = own_is_row ? xi : o;
+        const float dwi = -f.gw[i], dhj = -f.gh[j];
+        const float b = fmaf(dwi, f.hc[j], f.wc[i] * dhj), cc = dwi * dhj;
+        re = fmaf(f.step, b, fmaf(s2, cc, re));
+        r[e] = re;
+      }
+      acc = fmaf(re, __ldg(f.x + xi), acc);
+    }
+    for (int w = 16; w > 0; w >>= 1) acc += __shfl_xor_sync(kFull, acc, w);
+    if (lane == 0) {
+      const int slot = sg.slot[s];
+      if (slot < 0)
+        out[o] = fmaf(lam, f.own[o], acc);
+      else
+        partial[slot] = acc;
+    }
+  }
+}
+
 // part[3 b + q], q: |gw|^2, |gh|^2 contributions, then the 4 line-search sums
 __global__ void __launch_bounds__(kThreads) k_norm2_part(const float* __restrict__ a, int64_t na,
                                                         const float* __restrict__ b, int64_t nb,
@@ -198,6 +223,10 @@ BcdState& state(bm_ctx& h) {
   s.hc.alloc(ix.n);
   s.gw.alloc(ix.m);
   s.gh.alloc(ix.n);
+  s.wn.alloc(ix.m);
+  s.hn.alloc(ix.n);
+  s.gwn.alloc(ix.m);
+  s.ghn.alloc(ix.n);
   s.segs4.alloc(4 * (size_t)std::max<int64_t>(ix.rs.nseg, 1));
   s.part.alloc(4 * (size_t)parts_n() + 8);
   s.out.alloc(8);
@@ -208,15 +237,16 @@ int grid1(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(n, 1), 256), (int64_t)num_sms() * 8));
 }
 
-void col_spmv(bm_ctx& h, const Segs& sg, const int32_t* idx, const float* r, const float* x, const float* own,
-              float* out) {
+// residual update of the block in `cur` (if update) + block gradient into `out`
+void col_update_spmv(bm_ctx& h, const Segs& sg, const int32_t* idx, bool own_is_row, float* r, const FusedCols& f,
+                     float* out) {
   BM_REQUIRE((int64_t)h.sc.partial.n >= sg.nslots, BM_ERR_INVALID, "column solver: partial buffer too small");
   if (sg.nseg)
-    BM_LAUNCH(h, "bcd_spmv", k_col_spmv<<<seg_grid(sg.nseg), kThreads, 0, h.stream>>>(
-                                 view(sg), idx, r, x, own, (float)h.lambda, out, h.sc.partial.get()));
+    BM_LAUNCH(h, "bcd_update_spmv", k_col_update_spmv<<<seg_grid(sg.nseg), kThreads, 0, h.stream>>>(
+                                        view(sg), idx, own_is_row, r, f, (float)h.lambda, out, h.sc.partial.get()));
   if (sg.nmulti)
     BM_LAUNCH(h, "bcd_fixup", k_col_fixup<<<grid1(sg.nmulti), 256, 0, h.stream>>>(
-                                  sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti, h.sc.partial.get(), own,
+                                  sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti, h.sc.partial.get(), f.own,
                                   (float)h.lambda, out));
 }
 
@@ -236,45 +266,56 @@ double bcd_phase_dev(bm_ctx& h, int epochs, double* F_out) {
   }
   BcdState& s = state(h);
   const int parts = parts_n();
-  for (int ep = 0; ep < epochs; ++ep) {
-    for (int c = 0; c < h.k; ++c) {
-      BM_LAUNCH(h, "bcd_col", k_col_get<<<grid1(ix.m), 256, 0, h.stream>>>(h.W.get(), h.ld, c, ix.m, s.wc.get()));
-      BM_LAUNCH(h, "bcd_col", k_col_get<<<grid1(ix.n), 256, 0, h.stream>>>(h.H.get(), h.ld, c, ix.n, s.hc.get()));
-      // block gradients g_w = R h_c + lam w_c (rows), g_h = R^T w_c + lam h_c (columns)
-      col_spmv(h, ix.rs, ix.col.get(), h.r_csr.get(), s.hc.get(), s.wc.get(), s.gw.get());
-      col_spmv(h, ix.cs, ix.row.get(), h.r_csc.get(), s.wc.get(), s.hc.get(), s.gh.get());
-      // G = |g_w|^2 + |g_h|^2 and the line-search sums
-      BM_LAUNCH(h, "bcd_norm", k_norm2_part<<<parts, kThreads, 0, h.stream>>>(s.gw.get(), ix.m, s.gh.get(), ix.n,
-                                                                              s.part.get()));
-      BM_LAUNCH(h, "bcd_norm", k_rows_sum<<<1, kThreads, 0, h.stream>>>(s.part.get(), parts, 1, s.out.get()));
-      BM_LAUNCH(h, "bcd_ls", k_col_ls<<<seg_grid(ix.rs.nseg), kThreads, 0, h.stream>>>(
-                                 view(ix.rs), ix.col.get(), h.r_csr.get(), s.wc.get(), s.hc.get(), s.gw.get(),
-                                 s.gh.get(), s.segs4.get()));
-      BM_LAUNCH(h, "bcd_ls", k_rows_sum<<<1, kThreads, 0, h.stream>>>(s.segs4.get(), ix.rs.nseg, 4, s.out.get() + 1));
-      double o[5];
-      BM_CUDA(cudaMemcpyAsync(o, s.out.get(), 5 * sizeof(double), cudaMemcpyDeviceToHost, h.stream));
-      BM_CUDA(cudaStreamSynchronize(h.stream));
-      const double G = o[0];
-      double q[5] = {F, -G, 0.5 * o[1] + 0.5 * h.lambda * G, o[2], 0.5 * o[3]};
-      BM_REQUIRE(std::isfinite(G) && std::isfinite(q[2]), BM_ERR_NUMERIC, "column solver: non-finite sums");
-      const double st = quartic_argmin_ext(q);
-      if (st > 0) {
-        const float sf = (float)st;
-        BM_LAUNCH(h, "bcd_update", k_col_update<<<seg_grid(ix.rs.nseg), kThreads, 0, h.stream>>>(
-                                       view(ix.rs), ix.col.get(), true, h.r_csr.get(), s.wc.get(), s.hc.get(),
-                                       s.gw.get(), s.gh.get(), sf));
-        BM_LAUNCH(h, "bcd_update", k_col_update<<<seg_grid(ix.cs.nseg), kThreads, 0, h.stream>>>(
-                                       view(ix.cs), ix.row.get(), false, h.r_csc.get(), s.wc.get(), s.hc.get(),
-                                       s.gw.get(), s.gh.get(), sf));
-        BM_LAUNCH(h, "bcd_axpy", k_col_axpy<<<grid1(ix.m), 256, 0, h.stream>>>(h.W.get(), h.ld, c, ix.m, s.gw.get(),
-                                                                              -sf));
-        BM_LAUNCH(h, "bcd_axpy", k_col_axpy<<<grid1(ix.n), 256, 0, h.stream>>>(h.H.get(), h.ld, c, ix.n, s.gh.get(),
-                                                                              -sf));
-        F = (((q[4] * st + q[3]) * st + q[2]) * st + q[1]) * st + q[0];
-        h.bm_changed = true;
-        h.bf_dirty = true;
-      }
+  // Per block: the block gradient (for the first block its own two passes;
+  // afterwards fused with the previous block's residual update), the
+  // line-search sums, one read-back of five scalars, the column updates.
+  float *wc = s.wc.get(), *hc = s.hc.get(), *gw = s.gw.get(), *gh = s.gh.get();
+  float *wn = s.wn.get(), *hn = s.hn.get(), *gwn = s.gwn.get(), *ghn = s.ghn.get();
+  float prev_step = 0.f;
+  const int total = epochs * h.k;
+  for (int b = 0; b < total; ++b) {
+    const int c = b % h.k;
+    BM_LAUNCH(h, "bcd_col", k_col_get<<<grid1(ix.m), 256, 0, h.stream>>>(h.W.get(), h.ld, c, ix.m, wn));
+    BM_LAUNCH(h, "bcd_col", k_col_get<<<grid1(ix.n), 256, 0, h.stream>>>(h.H.get(), h.ld, c, ix.n, hn));
+    // block gradients g_w = R h_c + lam w_c (rows), g_h = R^T w_c + lam h_c (columns), after
+    // the previous block's residual update in the same passes
+    FusedCols fr{wc, hc, gw, gh, prev_step, b > 0 && prev_step > 0.f, hn, wn};
+    FusedCols fc{wc, hc, gw, gh, prev_step, b > 0 && prev_step > 0.f, wn, hn};
+    col_update_spmv(h, ix.rs, ix.col.get(), true, h.r_csr.get(), fr, gwn);
+    col_update_spmv(h, ix.cs, ix.row.get(), false, h.r_csc.get(), fc, ghn);
+    std::swap(wc, wn);
+    std::swap(hc, hn);
+    std::swap(gw, gwn);
+    std::swap(gh, ghn);
+    // G = |g_w|^2 + |g_h|^2 and the line-search sums
+    BM_LAUNCH(h, "bcd_norm", k_norm2_part<<<parts, kThreads, 0, h.stream>>>(gw, ix.m, gh, ix.n, s.part.get()));
+    BM_LAUNCH(h, "bcd_norm", k_rows_sum<<<1, kThreads, 0, h.stream>>>(s.part.get(), parts, 1, s.out.get()));
+    BM_LAUNCH(h, "bcd_ls", k_col_ls<<<seg_grid(ix.rs.nseg), kThreads, 0, h.stream>>>(
+                               view(ix.rs), ix.col.get(), h.r_csr.get(), wc, hc, gw, gh, s.segs4.get()));
+    BM_LAUNCH(h, "bcd_ls", k_rows_sum<<<1, kThreads, 0, h.stream>>>(s.segs4.get(), ix.rs.nseg, 4, s.out.get() + 1));
+    double o[5];
+    BM_CUDA(cudaMemcpyAsync(o, s.out.get(), 5 * sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+    BM_CUDA(cudaStreamSynchronize(h.stream));
+    const double G = o[0];
+    double q[5] = {F, -G, 0.5 * o[1] + 0.5 * h.lambda * G, o[2], 0.5 * o[3]};
+    BM_REQUIRE(std::isfinite(G) && std::isfinite(q[2]), BM_ERR_NUMERIC, "column solver: non-finite sums");
+    const double st = quartic_argmin_ext(q);
+    prev_step = st > 0 ? (float)st : 0.f;
+    if (st > 0) {
+      const float sf = (float)st;
+      BM_LAUNCH(h, "bcd_axpy", k_col_axpy<<<grid1(ix.m), 256, 0, h.stream>>>(h.W.get(), h.ld, c, ix.m, gw, -sf));
+      BM_LAUNCH(h, "bcd_axpy", k_col_axpy<<<grid1(ix.n), 256, 0, h.stream>>>(h.H.get(), h.ld, c, ix.n, gh, -sf));
+      F = (((q[4] * st + q[3]) * st + q[2]) * st + q[1]) * st + q[0];
+      h.bm_changed = true;
+      h.bf_dirty = true;
     }
+  }
+  // the last block's residual update (the residual stays consistent with W, H)
+  if (prev_step > 0.f) {
+    BM_LAUNCH(h, "bcd_update", k_col_update<<<seg_grid(ix.rs.nseg), kThreads, 0, h.stream>>>(
+                                   view(ix.rs), ix.col.get(), true, h.r_csr.get(), wc, hc, gw, gh, prev_step));
+    BM_LAUNCH(h, "bcd_update", k_col_update<<<seg_grid(ix.cs.nseg), kThreads, 0, h.stream>>>(
+                                   view(ix.cs), ix.row.get(), false, h.r_csc.get(), wc, hc, gw, gh, prev_step));
   }
   BM_CUDA(cudaStreamSynchronize(h.stream));
   if (F_out) *F_out = F;
