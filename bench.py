@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "netflix"
 K_BENCH = 64
+LMSVD_TOL = 1e-5   # the library's default LmSVD stop tolerance (bm_default_options)
 
 
 def _load_peaks():
@@ -378,7 +379,7 @@ def cpu_baseline(p, mode, target_nnz=400_000):
     k = min(K_BENCH, ix.m)
     W, H = random_factors(ix.m, ix.n, k, seed=11, scale=0.1)
     W, H = W.astype(np.float64), H.astype(np.float64)
-    opt = O.Options()
+    opt = O.Options(lmsvd_tol=LMSVD_TOL)     # the library's default stop tolerance
     st = O.State(W=W, H=H, U_prev=O.orth(W)[0], U_prev2=None, u=None, psi=opt.psi0,
                  rank_hist=[k, k], prev_warm_cols=k + 1, t=0, bm_changed=True)
     t0 = time.perf_counter()
@@ -410,7 +411,7 @@ def run_reference(args):
     ix = O.build_index(m, n, rows, cols, vals.astype(np.float64))
     k = min(K_BENCH, ix.m)
     W, H = random_factors(ix.m, ix.n, k, seed=11, scale=0.1)
-    opt = O.Options()
+    opt = O.Options(lmsvd_tol=LMSVD_TOL)     # the library's default stop tolerance
     st = O.State(W=W.astype(np.float64), H=H.astype(np.float64), U_prev=O.orth(W.astype(np.float64))[0],
                  U_prev2=None, u=None, psi=opt.psi0, rank_hist=[k, k], prev_warm_cols=k + 1, t=0,
                  bm_changed=True)
@@ -434,9 +435,14 @@ def run_reference(args):
             "value": v, "unit": "nnz/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}-shaped sample: {ix.m}x{ix.n}, {ix.nnz} entries", "k": k},
+            "config": {"workload": (f"{p.name}-shaped {p.m}x{p.n}, nnz={p.nnz}, Zipf(1.2), "
+                                    f"ratings {int(p.vals.min())}..{int(p.vals.max())}"),
+                       "lambda": p.lam, "k": k,
+                       "step": "3 BM iterations + 1 inexact PG step" if args.mode == "cycle"
+                       else "one loss/gradient evaluation", "parallelism": "host cores, rank 0 only"},
             "cpu_baseline": {"value": v, "unit": "nnz/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{ix.m}x{ix.n} sub-matrix, {ix.nnz} entries"},
+                             "sample": (f"each step on a {ix.m}x{ix.n} sub-matrix with {ix.nnz} entries (a "
+                                        f"random subset of the short side with all its entries), scaled to nnz/s")},
             "e2e": {"value": v, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -489,11 +495,13 @@ def run_tto(args):
         t0 = time.perf_counter()
         if args.step_rule == 1:
             from oracle import sparsa_oracle as S
-            _, Fh, _ = S.solve_bb(ix, p.lam, 8, 64, O.Options(), S.BbOptions(), max_outer=2000, tol=0.0,
+            _, Fh, _ = S.solve_bb(ix, p.lam, 8, 64, O.Options(lmsvd_tol=args.lmsvd_tol or LMSVD_TOL),
+                                  S.BbOptions(), max_outer=2000, tol=0.0,
                                   F_target=target)
             cycles = len(Fh) - 1
         else:
-            _, oi = O.solve(ix, p.lam, 8, 64, O.Options(), max_outer=2000, tol=0.0, F_target=target)
+            _, oi = O.solve(ix, p.lam, 8, 64, O.Options(lmsvd_tol=args.lmsvd_tol or LMSVD_TOL), max_outer=2000,
+                            tol=0.0, F_target=target)
             cycles = oi.outer
         cpu = {"value": time.perf_counter() - t0, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"the same solve to the same target ({cycles} cycles)"}
@@ -764,7 +772,8 @@ def run_edm_solve(args):
         st = E.EdmState(V=V, U=np.zeros((p.n, 0)), k_eig=min(k_max, V.shape[1] + 1))
         t0 = time.perf_counter()
         Vb, _ = E.bm_phase(st.V, i, j, d, w, lam, epochs)
-        E.prox_step(E.EdmState(V=Vb, U=st.U, k_eig=st.k_eig), i, j, d, w, lam, alpha, k_max, O.Options())
+        E.prox_step(E.EdmState(V=Vb, U=st.U, k_eig=st.k_eig), i, j, d, w, lam, alpha, k_max,
+                    O.Options(lmsvd_tol=LMSVD_TOL))
         el = time.perf_counter() - t0
         cpu = {"value": 1.0 / el, "unit": "cycles/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"one cycle of the same workload from the GPU's last factor, {el:.1f} s"}
