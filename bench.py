@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -225,7 +226,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")
+    clk_path = os.path.join(tempfile.gettempdir(), f"bm_bench_clocks_r{rank}_{os.getpid()}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     sampler, fh = _clock_sampler(clk_path)
     B.bm_profile_enable(h, True)
@@ -702,7 +703,7 @@ def run_edm_solve(args):
 
     for _ in range(args.warmup):
         F_hist.append(cycle()["F"])
-    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_edm_solve.csv")
+    clk_path = os.path.join(tempfile.gettempdir(), f"bm_bench_clocks_edm_{os.getpid()}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     sampler, fh = _clock_sampler(clk_path)
     torch.cuda.synchronize()

@@ -930,21 +930,6 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
     return;
   }
   const bool dbl = mode != kEigFast;
-  if (!dbl && n <= kJacMax && getenv("BM_EIG_JACOBI")) {
-    // FP32: parallel Jacobi (one block, both matrices in shared memory)
-    const int np = n + (n & 1);
-    const size_t smem = (size_t)2 * np * np * sizeof(float);
-    w.status.alloc(1);
-    BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
-    allow_max_smem((const void*)k_jacobi_eig<float>);
-    BM_LAUNCH(h, "jacobi_eig_f32",
-              k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S, n, 30, 1e-7f, evals, evecs, w.status.get()));
-    int st = 0;
-    BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
-    BM_CUDA(cudaStreamSynchronize(h.stream));
-    BM_REQUIRE(!(st & 2), BM_ERR_NUMERIC, "eigensolver: non-finite eigenvalue");
-    return;  // (st & 4: sweep cap reached; the FP32 result is still a valid near-diagonalisation)
-  }
   const size_t es = dbl ? 8 : 4;
   const size_t nn = (size_t)n * n * es;
   const size_t cap = 200 * 1024;
