@@ -15,7 +15,8 @@ def B():
     return B
 
 
-@pytest.mark.parametrize("n,k,weighted", [(3000, 3, False), (3000, 16, True), (5000, 7, True), (800, 33, False)])
+@pytest.mark.parametrize("n,k,weighted", [(3000, 3, False), (3000, 16, True), (5000, 7, True), (800, 33, False),
+                                          (30_000, 16, False)])   # the last: the 30,000-point chain itself
 def test_edm_parity(B, n, k, weighted):
     p = self_avoiding_chain(n=n, seed=n + k)
     rng = np.random.default_rng(k)
