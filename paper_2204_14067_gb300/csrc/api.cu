@@ -600,7 +600,7 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
     // F(X_t) is read from the first loss pass of each BM phase; the BM output
     // X~_t (F from its line search) is an iterate too and may end the solve.
     double F_prev = 0.0, F = 0.0;
-    bool have_prev = false, ended_on_bm = false;
+    bool have_prev = false;
     int outer = 0;
     for (outer = 1; outer <= so.max_outer; ++outer) {
       double F_bm = 0.0;
@@ -615,7 +615,7 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
         // the BF16 noise level (relative change < 3e-3 or no decrease)
         if (h->opt.precision == 1 && !h->refine && (rel < 3e-3 || F >= F_prev)) h->refine = true;
       }
-      if (so.F_target > 0 && F_bm <= so.F_target) { converged = true; ended_on_bm = true; break; }
+      if (so.F_target > 0 && F_bm <= so.F_target) { converged = true; break; }
       F_prev = F;
       have_prev = true;
       for (int x = 0; x < h->opt.pg_steps; ++x) {
@@ -626,7 +626,6 @@ bm_status bm_solve(bm_handle h, const bm_solve_opts* o, bm_solve_info* info) {
       }
       if (so.time_limit_s > 0 && elapsed() > so.time_limit_s) { ++outer; break; }
     }
-    (void)ended_on_bm;
     F = objective_now(*h);
     if (!converged && so.F_target > 0 && F <= so.F_target) converged = true;
     if (info) {

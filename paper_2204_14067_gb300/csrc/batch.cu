@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(256) k_dots_batch(const DenseP* __restrict__ d
     __syncthreads();
   }
   if (threadIdx.x < 4) {
-    const int col = phase == 0 ? threadIdx.x : (threadIdx.x < 2 ? P_GD + threadIdx.x : -1);
+    const int t = (int)threadIdx.x;
+    const int col = phase == 0 ? t : (t < 2 ? P_GD + t : -1);
     if (col >= 0) part[((int64_t)blockIdx.y * kSlabs + blockIdx.x) * 8 + col] = sh[threadIdx.x][0];
   }
 }

@@ -423,7 +423,8 @@ __global__ void k_col_sums(const float* __restrict__ U, int64_t n, int ld, doubl
 }
 
 // out(:, c) = a_out * out(:, c) + a * U(:, c) + b * colsum(c) / n
-__global__ void k_cols_combine(float* __restrict__ out, int ldo, const float* __restrict__ U, int ldu, int64_t n,
+// (out may be U itself: no __restrict__ on either)
+__global__ void k_cols_combine(float* out, int ldo, const float* U, int ldu, int64_t n,
                                int cols, float a_out, float a, const double* __restrict__ colsum, double b_over_n) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * cols; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / cols;

@@ -12,10 +12,6 @@
 namespace bm {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kPassThreads = 256;
-
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float dot4(float4 a, float4 b) {
   return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
 }
@@ -24,18 +20,6 @@ __device__ __forceinline__ void axpy4(float4& acc, float s, float4 x) {
   acc.y = fmaf(s, x.y, acc.y);
   acc.z = fmaf(s, x.z, acc.z);
   acc.w = fmaf(s, x.w, acc.w);
-}
-__device__ __forceinline__ float4 shfl_xor4(float4 v, int m) {
-  v.x += __shfl_xor_sync(kFull, v.x, m);
-  v.y += __shfl_xor_sync(kFull, v.y, m);
-  v.z += __shfl_xor_sync(kFull, v.z, m);
-  v.w += __shfl_xor_sync(kFull, v.w, m);
-  return v;
-}
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
 }
 
 // Rows split over several segments: out_i = sum of partials (segment order) + lam own_i
