@@ -56,3 +56,14 @@ def test_single_process_is_its_own_job():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.replica_throughput(None, 10.0, 500) == (10.0, 500.0, 50000.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun every rank but 0 exits at once without work or output."""
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1"],
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
