@@ -278,7 +278,8 @@ bm_status bm_get_panels(bm_handle h, int32_t* panels);
  * search) of all handles with the same row width is one launch over their
  * concatenated segment lists, and the direction, step length and update run
  * as batched device kernels, so an epoch is one CUDA graph replay (captured
- * on first use and re-captured when a rank changes).  F (double[count],
+ * on first use and re-captured when a rank, the work split or a buffer it
+ * captured changes).  F (double[count],
  * nullable) receives each handle's objective after the last iteration.
  * The batch owns a stream; the handles' own streams are synchronised first.
  * A handle must not be used elsewhere while its batch call runs, and must
@@ -313,7 +314,7 @@ typedef struct {
   int32_t workers;       /* host threads for the PG steps */
   double mem_budget_gb;  /* admission budget (0: device size) */
   int32_t max_outer;     /* cycles per solve */
-  int32_t pad_;
+  int32_t keep_factors;  /* 1: keep each finished solve's factors for bm_server_factors */
   double tol;            /* relative change of F that ends a solve */
 } bm_server_opts;
 typedef struct {
@@ -334,6 +335,15 @@ bm_status bm_server_submit(bm_server s, int64_t m, int64_t n, int64_t nnz, const
 bm_status bm_server_drain(bm_server s, double timeout_s);
 /* Copy up to cap results (completion order); *count receives the number finished. */
 bm_status bm_server_results(bm_server s, bm_request_result* out, int32_t cap, int32_t* count);
+/*
+ * With keep_factors = 1 the server copies each successfully finished solve's
+ * factors to host memory before it frees the solve's device state.
+ * bm_server_factors copies request id's factors (caller orientation, the
+ * request's m x k and n x k, row-major) into W float[m*k] and H float[n*k]
+ * and releases the server's copy; with W = H = NULL it only reports *k and
+ * keeps the copy.  BM_ERR_INVALID if no factors are kept for id.
+ */
+bm_status bm_server_factors(bm_server s, int64_t id, int32_t* k, float* W, float* H);
 double bm_server_now(bm_server s);
 const char* bm_server_last_error(bm_server s);
 void bm_server_destroy(bm_server s);
@@ -430,7 +440,9 @@ bm_status bm_edm_profile_read(bm_edm_handle h, int32_t cap, char* names, int64_t
  *   row_ptr   int64[m+1], col int32[nnz], val float[nnz]: CSR of Omega and A
  *             (columns < n; the arrays are trusted, not validated).
  *   W, H      float[m*ld], float[n*ld] row-major, 1 <= k <= ld <= 128,
- *             ld % 4 == 0; columns k..ld-1 must be zero.
+ *             ld % 4 == 0; columns k..ld-1 must be zero.  W, H and gW must
+ *             start on a 16-byte boundary (rows are moved as float4), else
+ *             BM_ERR_INVALID; lambda must be finite in FP32.
  *   gW        float[m*ld] out: R H + lambda W (columns k..ld-1 written as 0).
  *   f         double* out (device): 1/2 sum r_e^2.
  *   stream    cudaStream_t the work is queued on (NULL: default stream).

@@ -518,7 +518,7 @@ def bm_batch_bm_phase(b, count, epochs):
 class bm_server_opts(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int32), ("precision", ctypes.c_int32), ("batched", ctypes.c_int32),
                 ("workers", ctypes.c_int32), ("mem_budget_gb", ctypes.c_double), ("max_outer", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("tol", ctypes.c_double)]
+                ("keep_factors", ctypes.c_int32), ("tol", ctypes.c_double)]
 
 
 class bm_request_result(ctypes.Structure):
@@ -533,6 +533,7 @@ _SIGS.update({
                                     _P]),
     "bm_server_drain": (_c.c_int, [_P, _c.c_double]),
     "bm_server_results": (_c.c_int, [_P, _P, _c.c_int32, _P]),
+    "bm_server_factors": (_c.c_int, [_P, _c.c_int64, _P, _P, _P]),
     "bm_server_now": (_c.c_double, [_P]),
     "bm_server_last_error": (_c.c_char_p, [_P]),
     "bm_server_destroy": (None, [_P]),
@@ -546,9 +547,9 @@ def _check_server(status: int, s=None):
 
 
 def bm_server_create(max_active=16, precision=0, batched=1, workers=8, mem_budget_gb=0.0, max_outer=100,
-                     tol=1e-6):
+                     tol=1e-6, keep_factors=0):
     o = bm_server_opts(max_active=max_active, precision=precision, batched=batched, workers=workers,
-                       mem_budget_gb=mem_budget_gb, max_outer=max_outer, tol=tol)
+                       mem_budget_gb=mem_budget_gb, max_outer=max_outer, tol=tol, keep_factors=keep_factors)
     s = _P()
     _check_server(lib().bm_server_create(ctypes.byref(o), ctypes.byref(s)))
     return s.value
@@ -571,6 +572,17 @@ def bm_server_results(s):
     arr = (bm_request_result * max(1, cnt.value))()
     _check_server(lib().bm_server_results(s, arr, cnt.value, ctypes.byref(cnt)), s)
     return [{n: getattr(arr[i], n) for n, _ in bm_request_result._fields_ if n != "pad_"} for i in range(cnt.value)]
+
+
+def bm_server_factors(s, rid, m, n):
+    """Factors (W m x k, H n x k, caller orientation) of finished request rid
+    (server created with keep_factors=1); the server's copy is released."""
+    k = ctypes.c_int32()
+    _check_server(lib().bm_server_factors(s, int(rid), ctypes.byref(k), None, None), s)
+    W = np.zeros((int(m), k.value), np.float32)
+    H = np.zeros((int(n), k.value), np.float32)
+    _check_server(lib().bm_server_factors(s, int(rid), ctypes.byref(k), _ptr(W), _ptr(H)), s)
+    return W, H
 
 
 def bm_server_now(s):

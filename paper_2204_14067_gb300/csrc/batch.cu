@@ -6,8 +6,8 @@
 // direction, the quartic line search and the update run as batched kernels
 // with one thread (or one block slice) per problem, reading their scalars from
 // device memory.  An epoch therefore needs no host round trip, is captured
-// once into a CUDA graph and replayed for every epoch while the set of
-// problems and their ranks stay the same.
+// once into a CUDA graph and replayed for every epoch while the problems'
+// ranks and the buffers the graph captured stay the same.
 #include <algorithm>
 #include <cmath>
 #include <memory>
@@ -271,7 +271,7 @@ struct bm_batch_ctx {
   int count = 0;
   cudaStream_t stream = nullptr;
   bool bf = false;
-  std::vector<int> ranks;            // ranks the tables / graph were built for
+  std::vector<uintptr_t> sig;        // ranks and device pointers the tables / graph were built for
   std::vector<std::unique_ptr<Group>> groups;
   DevBuf<DenseP> dense;
   DevBuf<FixP> fix_csr, fix_csc;
@@ -408,6 +408,29 @@ void build_tables(bm_batch_ctx& b) {
   BM_CUDA(cudaStreamSynchronize(b.stream));
 }
 
+// What the tables and the captured graph of one handle depend on: its rank,
+// precision state, sizes and every device pointer build_tables() records.
+void append_signature(const bm_ctx& h, std::vector<uintptr_t>& sig) {
+  const Index& ix = h.ix;
+  const uintptr_t v[] = {(uintptr_t)h.k, (uintptr_t)h.ld, (uintptr_t)h.bf_active(), (uintptr_t)ix.m,
+                         (uintptr_t)ix.n, (uintptr_t)ix.nnz, (uintptr_t)ix.codec,
+                         (uintptr_t)h.W.get(), (uintptr_t)h.H.get(), (uintptr_t)h.gW.get(), (uintptr_t)h.gH.get(),
+                         (uintptr_t)h.DW.get(), (uintptr_t)h.DH.get(), (uintptr_t)h.gWp.get(),
+                         (uintptr_t)h.gHp.get(), (uintptr_t)h.Wb.get(), (uintptr_t)h.Hb.get(),
+                         (uintptr_t)h.DHb.get(), (uintptr_t)h.r_csr.get(), (uintptr_t)h.sc.fseg.get(),
+                         (uintptr_t)h.sc.partial.get(), (uintptr_t)ix.col.get(), (uintptr_t)ix.row.get(),
+                         (uintptr_t)ix.val.get(), (uintptr_t)ix.cval.get(), (uintptr_t)ix.val8.get(),
+                         (uintptr_t)ix.cval8.get()};
+  sig.insert(sig.end(), std::begin(v), std::end(v));
+  for (int kind : {kPassGradCsr, kPassGradCsc, kPassLsCsr}) {
+    const Segs& sg = pass_segs(ix, kind);
+    const uintptr_t w[] = {(uintptr_t)sg.nseg, (uintptr_t)sg.nmulti, (uintptr_t)sg.row.get(),
+                           (uintptr_t)sg.beg.get(), (uintptr_t)sg.end.get(), (uintptr_t)sg.slot.get(),
+                           (uintptr_t)sg.mrow.get(), (uintptr_t)sg.mfirst.get(), (uintptr_t)sg.mcount.get()};
+    sig.insert(sig.end(), std::begin(w), std::end(w));
+  }
+}
+
 int grid_for_work(int64_t work) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), (int64_t)num_sms() * 8));
 }
@@ -527,20 +550,21 @@ bm_status bm_batch_bm_phase(bm_batch b, int32_t epochs, double* F) {
   if (!b) return BM_ERR_INVALID;
   return batch_guarded(b, [&] {
     BM_REQUIRE(epochs >= 0, BM_ERR_INVALID, "bm_batch_bm_phase: epochs must be >= 0");
-    std::vector<int> ranks(b->count);
+    std::vector<uintptr_t> sig;
     for (int p = 0; p < b->count; ++p) {
       bm_ctx& h = *b->hs[p];
       BM_CUDA(cudaStreamSynchronize(h.stream));
       BM_REQUIRE(h.k >= 1, BM_ERR_INVALID, "bm_batch_bm_phase: every handle needs rank >= 1 (run bm_init)");
-      ranks[p] = h.k * 2 + (h.bf_active() ? 1 : 0);
       if (b->bf) {
         BM_REQUIRE(h.Wb.get() && h.DHb.get(), BM_ERR_INVALID, "bm_batch_bm_phase: BF16 copies missing");
       }
+      append_signature(h, sig);
     }
-    if (ranks != b->ranks || !b->exec) {
+    // rebuild the tables and the graph when a rank or any buffer they captured changed
+    if (sig != b->sig || !b->exec) {
       drop_graph(*b);
       build_tables(*b);
-      b->ranks = ranks;
+      b->sig = sig;
       BM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       try {
         enqueue_epoch(*b);

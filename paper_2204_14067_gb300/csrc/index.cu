@@ -294,7 +294,7 @@ __global__ void k_lower_bounds(const uint64_t* __restrict__ keys, int64_t nnz, u
 }
 
 int grid_for(int64_t n, int threads) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), 4 * 152 * 8));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), (int64_t)num_sms() * 32));
 }
 
 // bounds[i * (P + 1) + p] = first entry of row i whose index is >= p * pw

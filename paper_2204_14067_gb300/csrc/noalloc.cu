@@ -168,11 +168,18 @@ bm_status bm_loss_grad_csr_noalloc(int64_t m, int64_t n, const int64_t* row_ptr,
     return fail(BM_ERR_INVALID, "bm_loss_grad_csr_noalloc: m exceeds BM_NOALLOC_MAX_ROWS (262144 rows)");
   if (k < 1 || k > 128 || ld < k || (ld & 3) || ld > 128)
     return fail(BM_ERR_INVALID, "bm_loss_grad_csr_noalloc: need 1 <= k <= 128 and k <= ld <= 128, ld % 4 == 0");
-  if (!std::isfinite(lambda)) return fail(BM_ERR_INVALID, "bm_loss_grad_csr_noalloc: lambda must be finite");
+  // lambda is used in FP32: a finite double above FLT_MAX would become inf
+  if (!std::isfinite(lambda) || !std::isfinite((float)lambda))
+    return fail(BM_ERR_INVALID, "bm_loss_grad_csr_noalloc: lambda must be finite in FP32");
   const void* ptrs[] = {row_ptr, col, val, W, H, gW, f};
   for (const void* p : ptrs)
     if (!p || !on_device(p))
       return fail(BM_ERR_INVALID, "bm_loss_grad_csr_noalloc: every array must be a device pointer");
+  // the factor rows are read and the gradient rows written as float4
+  if (((uintptr_t)W | (uintptr_t)H | (uintptr_t)gW) & 15)
+    return fail(BM_ERR_INVALID, "bm_loss_grad_csr_noalloc: W, H and gW must be 16-byte aligned");
+  if (((uintptr_t)row_ptr | (uintptr_t)f) & 7 || ((uintptr_t)col | (uintptr_t)val) & 3)
+    return fail(BM_ERR_INVALID, "bm_loss_grad_csr_noalloc: misaligned row_ptr, col, val or f");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();

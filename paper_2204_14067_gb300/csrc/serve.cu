@@ -9,11 +9,13 @@
 // while others are on the GPU join at the next cycle; finished solves leave
 // and free their slot and memory.  The plain mode runs one solve at a time
 // with bm_solve.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -47,8 +49,14 @@ thread_local std::string g_server_error;
 
 }  // namespace
 
+struct KeptFactors {
+  int32_t k = 0;
+  std::vector<float> W, H;   // caller orientation, m x k and n x k
+};
+
 struct bm_server_ctx {
   bm_server_opts o{};
+  std::map<int64_t, KeptFactors> kept;   // keep_factors: finished solves' factors by request id
   Clock::time_point t0;
   std::mutex mu;
   std::condition_variable cv;
@@ -97,9 +105,20 @@ void finish(bm_server_ctx& s, Active& a, bm_status st) {
   r.t_submit = a.req.t_submit;
   r.t_start = a.t_start;
   r.t_done = s.now();
+  KeptFactors kf;
+  bool keep = false;
+  if (s.o.keep_factors && st == BM_OK && a.h) {
+    kf.k = k;
+    kf.W.resize((size_t)a.req.m * k);
+    kf.H.resize((size_t)a.req.n * k);
+    int32_t kk = 0;
+    if (bm_get_factors(a.h, &kk, kf.W.data(), kf.H.data()) == BM_OK && kk == k) keep = true;
+    else r.status = BM_ERR_CUDA;
+  }
   if (a.h) bm_destroy(a.h);
   a.h = nullptr;
   std::lock_guard<std::mutex> lk(s.mu);
+  if (keep) s.kept[r.id] = std::move(kf);
   s.mem_used -= a.mem;
   s.done.push_back(r);
   s.in_system--;
@@ -223,14 +242,25 @@ void run_batched(bm_server_ctx& s) {
       });
     }
     for (auto& t : pool) t.join();
-    // retire finished solves
+    // retire finished solves.  A batch must not outlive its handles: when a
+    // member retires the batch is destroyed first (a later bm_create may
+    // return the freed handle's address, so the handle list alone cannot
+    // tell an old batch from a new one).
     std::vector<Active> keep;
     for (size_t i = 0; i < act.size(); ++i) {
       Active& a = act[i];
       const bool conv = std::isfinite(a.F_prev) && (a.h->opt.precision == 0 || a.h->refine) &&
                         std::fabs(a.F_prev - a.F) / (1.0 + std::fabs(a.F_prev)) < s.o.tol;
-      if (sts[i] != BM_OK || conv || a.outer >= s.o.max_outer) finish(s, a, sts[i]);
-      else keep.push_back(std::move(a));
+      if (sts[i] != BM_OK || conv || a.outer >= s.o.max_outer) {
+        if (bt && std::find(bt_set.begin(), bt_set.end(), a.h) != bt_set.end()) {
+          bm_batch_destroy(bt);
+          bt = nullptr;
+          bt_set.clear();
+        }
+        finish(s, a, sts[i]);
+      } else {
+        keep.push_back(std::move(a));
+      }
     }
     act.swap(keep);
   }
@@ -243,8 +273,9 @@ extern "C" {
 
 bm_status bm_server_create(const bm_server_opts* o, bm_server* out) {
   if (!o || !out) return BM_ERR_INVALID;
-  if (o->max_active < 1 || o->max_outer < 1 || (o->precision != 0 && o->precision != 1)) {
-    g_server_error = "bm_server_create: max_active, max_outer >= 1 and precision 0 or 1 required";
+  if (o->max_active < 1 || o->max_outer < 1 || (o->precision != 0 && o->precision != 1) ||
+      (o->keep_factors != 0 && o->keep_factors != 1)) {
+    g_server_error = "bm_server_create: max_active, max_outer >= 1, precision and keep_factors 0 or 1 required";
     return BM_ERR_INVALID;
   }
   bm_server_ctx* s = new bm_server_ctx();
@@ -305,6 +336,22 @@ bm_status bm_server_results(bm_server s, bm_request_result* out, int32_t cap, in
   std::lock_guard<std::mutex> lk(s->mu);
   if (count) *count = (int32_t)s->done.size();
   for (int32_t i = 0; out && i < cap && i < (int32_t)s->done.size(); ++i) out[i] = s->done[i];
+  return BM_OK;
+}
+
+bm_status bm_server_factors(bm_server s, int64_t id, int32_t* k, float* W, float* H) {
+  if (!s) return BM_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->kept.find(id);
+  if (it == s->kept.end()) {
+    s->err = "bm_server_factors: no factors kept for request " + std::to_string(id);
+    return BM_ERR_INVALID;
+  }
+  if (k) *k = it->second.k;
+  if (!W && !H) return BM_OK;
+  if (W) std::copy(it->second.W.begin(), it->second.W.end(), W);
+  if (H) std::copy(it->second.H.begin(), it->second.H.end(), H);
+  s->kept.erase(it);
   return BM_OK;
 }
 

@@ -1,14 +1,16 @@
 """GPU parity of the index build and the sparse loss/gradient against the FP64 oracle.
 
-Index work must be bit-exact.  Floats: f, F within 1e-5 relative, gradients
-within 1e-5 in relative Frobenius norm (FP32 arithmetic with FP64 final
-reductions against FP64).
+Index work must be bit-exact.  Floats: f, F within 1e-5 relative; gradients
+row by row within 1e-5 (tests/parity.py: every row's error against the row's
+norm plus a small floor) and within 1e-5 in relative Frobenius norm (FP32
+arithmetic with FP64 final reductions against FP64).
 """
 import numpy as np
 import pytest
 
 from oracle import bm_oracle as O
 from synth import named_config, planted_uniform, random_factors
+from tests.parity import assert_rows_close, grad_rounding_scales
 
 pytestmark = pytest.mark.gpu
 
@@ -110,13 +112,21 @@ def test_loss_grad_parity(B, k, shape):
         ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
         W64, H64 = W.astype(np.float64), H.astype(np.float64)
         Wi, Hi = (H64, W64) if ix.transposed else (W64, H64)
-        fo, Fo, gWo, gHo, _ = O.loss_grad(ix, Wi, Hi, p.lam)
+        fo, Fo, gWo, gHo, r = O.loss_grad(ix, Wi, Hi, p.lam)
+        aW, aH = grad_rounding_scales(ix, r, Wi, Hi, p.lam)
         if ix.transposed:
-            gWo, gHo = gHo, gWo
+            gWo, gHo, aW, aH = gHo, gWo, aH, aW
         assert abs(f - fo) <= RTOL * fo
         assert abs(F - Fo) <= RTOL * Fo
         assert _rel(gW, gWo) <= RTOL
         assert _rel(gH, gHo) <= RTOL
+        assert_rows_close(gW, gWo, RTOL, what="gW", extra=aW)
+        assert_rows_close(gH, gHo, RTOL, what="gH", extra=aH)
+        # the cases cover rows split over three or more segments (1,024
+        # entries each) and short rows and columns
+        deg_r, deg_c = np.diff(ix.row_ptr), np.diff(ix.col_ptr)
+        if shape[0] == 20_000:
+            assert deg_r.max() > 2 * 1024 and deg_c.min() <= 40
     finally:
         B.bm_destroy(h)
 

@@ -10,6 +10,7 @@ import pytest
 
 from oracle import bm_oracle as O
 from synth import named_config, random_factors
+from tests.parity import assert_rows_close, grad_rounding_scales
 
 pytestmark = pytest.mark.gpu
 
@@ -32,10 +33,11 @@ def prob():
 def _oracle_grad(p, W, H):
     ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
     Wi, Hi = (H, W) if ix.transposed else (W, H)
-    f, F, gW, gH, _ = O.loss_grad(ix, Wi.astype(np.float64), Hi.astype(np.float64), p.lam)
+    f, F, gW, gH, r = O.loss_grad(ix, Wi.astype(np.float64), Hi.astype(np.float64), p.lam)
+    aW, aH = grad_rounding_scales(ix, r, Wi, Hi, p.lam)
     if ix.transposed:
-        gW, gH = gH, gW
-    return ix, f, F, gW, gH
+        gW, gH, aW, aH = gH, gW, aH, aW
+    return ix, f, F, gW, gH, aW, aH
 
 
 @pytest.mark.parametrize("panels", [[1, 1, 1, 1, 1], [2, 3, 4, 5, 6], [16, 16, 16, 16, 16], [7, 1, 3, 1, 9]])
@@ -43,7 +45,7 @@ def test_loss_grad_any_panels(B, prob, panels):
     p = prob
     k = 33
     W, H = random_factors(p.m, p.n, k, seed=3, scale=0.3)
-    _, f_o, F_o, gW_o, gH_o = _oracle_grad(p, W, H)
+    _, f_o, F_o, gW_o, gH_o, aW, aH = _oracle_grad(p, W, H)
     h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 64)
     try:
         B.bm_set_panels(h, panels)
@@ -54,6 +56,8 @@ def test_loss_grad_any_panels(B, prob, panels):
         assert abs(f - f_o) <= RTOL * f_o and abs(F - F_o) <= RTOL * F_o
         assert np.linalg.norm(gW - gW_o) <= RTOL * np.linalg.norm(gW_o)
         assert np.linalg.norm(gH - gH_o) <= RTOL * np.linalg.norm(gH_o)
+        assert_rows_close(gW, gW_o, RTOL, what="gW", extra=aW)
+        assert_rows_close(gH, gH_o, RTOL, what="gH", extra=aH)
         # a fixed split is deterministic
         gW2, gH2 = np.empty_like(W), np.empty_like(H)
         f2, _ = B.bm_loss_grad(h, gW2, gH2)
