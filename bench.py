@@ -1,20 +1,24 @@
 """Benchmark of the BM-Global hot path on one GB300 (or N independent replicas).
 
-One step = one cycle of Algorithm 1 on the recommendation-scale workload
-(480,189 x 17,770, 100,480,507 Zipf(1.2) ratings, lambda = 0.25, k = 64):
-3 BM iterations (loss/gradient pass + exact line-search pass + update) and one
-inexact proximal-gradient step (LmSVD on L(U) = Z Z^T U, exact small SVD,
-soft-threshold, refactor).  `value` counts observed entries processed per
-second per cycle (nnz / cycle time) summed over replicas.
+Default (`--mode grad`): one step = one evaluation of the loss and both
+gradients (bm_loss_grad: the SDDMM residual and the SpMMs R H and R^T W) on
+the recommendation-scale workload (480,189 x 17,770, 100,480,507 Zipf(1.2)
+ratings, lambda = 0.25, k = 64, FP32); `value` = observed entries per second
+summed over replicas ("BM gradient nnz/s").  The line carries the roofline of
+the dominant pass (against the FP32 ALU and HBM peaks and against the measured
+gather roof of its index order), the whole call's fractions, the FP64
+oracle's rate on the host cores, an end-to-end figure through host buffers,
+and secondary figures: cycles of Algorithm 1 on the same handle, time to the
+oracle's objective on the planted 500 x 300 problem, a serving sample.
 
-`--mode grad` times bm_loss_grad alone (the SDDMM + two SpMM passes).
-`--mode tto` times a solve to the FP64 oracle's objective on the planted
-500 x 300 problem; `--mode serve` measures the continuous-batching server.
-`--mode edm` times the distance-geometry loss/gradient and `--mode edm_solve`
-the cycles of Algorithm 1 on the distance-geometry QSDP (30,000-point chain);
-`--mode bcd` compares the column-block BM solver with the PR+ BM phase.
-`--impl reference` times the FP64 oracle on the host cores on a bounded
-sample of the same workload.
+`--mode cycle` times cycles of Algorithm 1 (3 BM iterations + 1 inexact PG
+step) instead.  `--mode tto` times a solve to the FP64 oracle's objective on
+the planted 500 x 300 problem; `--mode serve` measures the continuous-batching
+server.  `--mode edm` times the distance-geometry loss/gradient and
+`--mode edm_solve` the cycles of Algorithm 1 on the distance-geometry QSDP
+(30,000-point chain); `--mode bcd` compares the column-block BM solver with
+the PR+ BM phase.  `--impl reference` times the FP64 oracle on the host cores
+on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -144,26 +148,6 @@ def algorithmic_bytes(kernel, d, k, q, vb=4):
     return None
 
 
-def measured_traffic(kernel, d, k, panels=1, codec=False):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary
-    (profiles/<kernel>_netflix_k<k>[_codec].txt: 'dram_bytes_per_launch: N'
-    taken with 'panels: P'), or None when no capture of the kernel as it runs
-    exists."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_netflix_k{k}{'_codec' if codec else ''}.txt")
-    got, cap_panels, cap_codec = None, None, 0
-    try:
-        for line in open(path):
-            if line.startswith("dram_bytes_per_launch:"):
-                got = float(line.split(":", 1)[1])
-            elif line.startswith("panels:"):
-                cap_panels = int(line.split(":", 1)[1])
-            elif line.startswith("value_codec:"):
-                cap_codec = int(line.split(":", 1)[1])
-    except OSError:
-        return None
-    return got if cap_panels == panels and cap_codec == int(codec) else None
-
-
 def algorithmic_flops(kernel, d, k, q):
     nnz = d["nnz"]
     if kernel in ("grad_csr", "grad_csc"):
@@ -206,6 +190,9 @@ def run_ours(args):
 
     gWd = torch.empty((p.m, k), dtype=torch.float32, device="cuda")
     gHd = torch.empty((p.n, k), dtype=torch.float32, device="cuda")
+    # gather roof of the gradient passes: a gather-only pass over the same
+    # index order (bm_gather_roof), outside the timed region
+    gather = {nm: B.bm_gather_roof(h, nm) for nm in ("grad_csr", "grad_csc")} if args.mode == "grad" else {}
 
     def step():
         if args.mode == "grad":
@@ -248,26 +235,62 @@ def run_ours(args):
     clocks = _clock_summary(clk_path, local)
     k_now = B.bm_dims(h)["k"]
 
-    # end to end through the public API with host buffers, copies inside the timed region
+    # end to end through the public API with host buffers, copies inside the
+    # timed region: grad mode copies the factors in and both gradients out;
+    # cycle mode copies the whole solve state (factors and the PG step's warm
+    # start) in and out, so every cycle runs from the state the last one left
     Wh = np.ascontiguousarray(W0)
     Hh = np.ascontiguousarray(H0)
     e2e_steps = max(1, min(args.steps, 3))
+    state = B.bm_get_state(h) if args.mode == "cycle" else None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    kk = k
+    h2d = d2h = 0
     for _ in range(e2e_steps):
-        B.bm_set_factors(h, kk, Wh, Hh)
         if args.mode == "grad":
+            B.bm_set_factors(h, k, Wh, Hh)
             gW = np.empty_like(Wh)
             gH = np.empty_like(Hh)
             B.bm_loss_grad(h, gW, gH)
+            h2d, d2h = Wh.nbytes + Hh.nbytes, gW.nbytes + gH.nbytes
         else:
+            B.bm_set_state(h, state)
             B.bm_solve(h, max_outer=1, tol=0.0)
-            Wh, Hh = B.bm_get_factors(h, p.m, p.n)
-            kk = Wh.shape[1]
+            h2d = len(state)
+            state = B.bm_get_state(h)
+            d2h = len(state)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    # secondary figures of the default (gradient) run: cycles of Algorithm 1
+    # on the same handle, time to the oracle's objective, a serving sample
+    extra = {}
+    if args.mode == "grad" and not args.no_extra:
+        B.bm_solve(h, max_outer=2, tol=0.0)
+        ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev2.record(stream)
+        B.bm_solve(h, max_outer=5, tol=0.0)
+        ev3.record(stream)
+        torch.cuda.synchronize()
+        cyc_ms = ev2.elapsed_time(ev3) / 5
+        extra["cycle"] = {"metric": "BM-Global cycle nnz/s", "value": p.nnz / (cyc_ms / 1e3), "unit": "nnz/s",
+                          "ms_per_cycle": cyc_ms, "cycles": 5, "k_end": B.bm_dims(h)["k"],
+                          "step": "3 BM iterations + 1 inexact PG step"}
     B.bm_destroy(h)
+    if args.mode == "grad" and not args.no_extra:
+        import types
+        sub = types.SimpleNamespace(**vars(args))
+        sub.steps, sub.warmup, sub.no_cpu = 1, 1, False
+        t = run_tto(sub)
+        extra["time_to_oracle"] = {"metric": t["metric"], "value": t["value"], "unit": "s",
+                                   "workload": t["config"]["workload"], "cycles": t["config"]["cycles"],
+                                   "final_rel": t["config"]["final_rel"], "e2e_s": t["e2e"]["value"],
+                                   "oracle_s": (t["cpu_baseline"] or {}).get("value")}
+        sub.serve_count = 16
+        sv = run_serve(sub)
+        extra["serving"] = {"metric": sv["metric"], "value": sv["value"], "unit": sv["unit"],
+                            "workload": sv["config"]["workload"], "batched_bf16": sv["batched_bf16"],
+                            "one_at_a_time_fp32": sv["one_at_a_time_fp32"], "final_objective": sv["final_objective"]}
 
     ms_step, total_units, value = replica_throughput(dist, ms / args.steps, p.nnz)
     e2e_val = _sumall(dist, float(p.nnz)) / _maxall(dist, e2e_s)
@@ -295,10 +318,10 @@ def run_ours(args):
     if avg_s and fl is not None and by is not None:
         intensity = fl / by
         ridge = alu_peak * 1e12 / (float(peaks["hbm_gbs"]) * 1e9)
-        traffic = measured_traffic(name, d, kk, tune[name][0] if tune and name in tune else 1,
-                                   codec_on and name in ("grad_csr", "grad_csc"))
-        if traffic is not None and p.name != WORKLOAD:
-            traffic = None   # the committed captures are of the netflix-shaped workload
+        # DRAM bytes of a full-size launch are not captured: the two DRAM
+        # counters take two ncu passes, and multi-pass captures run on the
+        # quarter-size case only (profiles/grad_sparse_netflix_quarter_k64.txt)
+        traffic = None
         if intensity >= ridge:
             ach = fl / avg_s / 1e12
             roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
@@ -315,6 +338,16 @@ def run_ours(args):
         roof["flops_per_launch"] = fl
         roof["avg_launch_ms"] = avg_s * 1e3
         roof["top_kernel_overall"] = top_all
+        roof["traffic_note"] = ("not captured at full size (two-pass counters); quarter-size case: "
+                                "profiles/grad_sparse_netflix_quarter_k64.txt")
+        if name in gather:
+            # the pass gathers one FP32 row per entry; the measured roof is a
+            # gather-only pass over the same index order
+            g_ms, g_gbs = gather[name]
+            gb = d["nnz"] * kk * 4
+            roof["l2_gather"] = {"achieved_gbs": gb / avg_s / 1e9, "peak_gbs": g_gbs, "frac": g_ms / (avg_s * 1e3),
+                                 "gathered_bytes_per_launch": gb,
+                                 "peak_source": "measured: gather-only pass over the same index (bm_gather_roof)"}
     # the whole loss/gradient call (every pass it launches) against both roofs
     grad_call = None
     if args.mode == "grad":
@@ -327,6 +360,12 @@ def run_ours(args):
                      "hbm_frac": by_call / s_call / 1e9 / float(peaks["hbm_gbs"]),
                      "alu_tflops": fl_call / s_call / 1e12, "alu_frac": fl_call / s_call / 1e12 / alu_peak,
                      "kernels": sorted(prof)}
+        if gather:
+            g_ms = sum(v[0] for v in gather.values())
+            grad_call["l2_gather"] = {"gather_only_ms": g_ms, "frac": g_ms / ms_step,
+                                      "gathered_bytes": 2 * d["nnz"] * k * 4,
+                                      "note": "both passes gather one FP32 factor row per entry; the roof is the "
+                                              "time of gather-only passes over the same index orders"}
     cpu = cpu_baseline(p, args.mode) if not args.no_cpu else None
     line = {
         "metric": "BM gradient nnz/s" if args.mode == "grad" else "BM-Global cycle nnz/s",
@@ -348,14 +387,16 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (1.6 GB of index per pass)",
                    "generate_s": round(t_gen, 1),
                    "value_codec": "one byte per observed value" if codec_on else "fp32 values",
-                   "panels": ({nm: v[0] for nm, v in tune.items()} if tune else "natural split")},
+                   "work_split": ({nm: {"panels": v[0], "layout": "warp per segment" if v[3] else "group per segment"}
+                                   for nm, v in tune.items()} if tune else "natural split, automatic layout")},
         "e2e": {"value": e2e_val, "unit": "nnz/s",
-                "h2d_bytes_per_step": int(W0.nbytes + H0.nbytes),
-                "d2h_bytes_per_step": int(W0.nbytes + H0.nbytes)},
+                "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(sum(v[0] for v in prof.values())) // max(1, args.steps) * args.steps,
         "kernels": {kname: {"launches": v[0], "ms": round(v[1], 4)} for kname, v in sorted(prof.items())},
         "roofline": roof,
         "gradient_call": grad_call,
+        "secondary": extra or None,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -816,6 +857,7 @@ def run_edm_solve(args):
         "kernels": {kname: {"launches": v[0], "ms": round(v[1], 4)} for kname, v in sorted(prof.items())},
         "roofline": roof,
         "gradient_call": grad_call,
+        "secondary": extra or None,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -908,6 +950,8 @@ def main():
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the natural work split (one panel)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="grad mode: skip the secondary figures (cycle, time to oracle, serving sample)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

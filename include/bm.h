@@ -250,7 +250,8 @@ bm_status bm_set_state(bm_handle h, const void* buf, size_t len);
  *
  * bm_autotune times every kind with one panel and, where the gathered block
  * exceeds a quarter of L2, with 2, 3, 4, 6, 8, 12, 16 panels (up to
- * max_panels), and keeps the fastest; it needs factors (k >= 1), overwrites
+ * max_panels), each in both kernel layouts (bm_set_layout), and keeps the
+ * fastest; it needs factors (k >= 1), overwrites
  * the gradient, search-direction and PG scratch buffers (not W, H or the PG
  * warm-start state) and takes about 20 launches per kind.  info (nullable)
  * receives the choice.  bm_set_panels fixes the counts (each in
@@ -264,11 +265,38 @@ typedef struct {
   int32_t panels[BM_PASS_KINDS];   /* chosen panel count per pass kind */
   int32_t timed;                   /* timed candidates */
   double ms[BM_PASS_KINDS];        /* one launch with the chosen split (ms, fastest of 3) */
-  double ms_single[BM_PASS_KINDS]; /* one launch with one panel (ms, fastest of 3) */
+  double ms_single[BM_PASS_KINDS]; /* one launch with one panel and the automatic layout (ms) */
+  int32_t layout[BM_PASS_KINDS];   /* chosen kernel layout per pass kind (see bm_set_layout) */
+  int32_t pad_;
 } bm_tune_info;
 bm_status bm_autotune(bm_handle h, int32_t max_panels, bm_tune_info* info);
 bm_status bm_set_panels(bm_handle h, const int32_t* panels);
 bm_status bm_get_panels(bm_handle h, int32_t* panels);
+/*
+ * Kernel layout of each pass kind: 0 = a group of lanes per segment (several
+ * segments per warp; suits many short rows or columns), 1 = a whole warp per
+ * segment (suits long ones), -1 = automatic (1 when the pass's segments hold
+ * 512 or more entries on average).  bm_autotune also times both layouts and
+ * keeps the faster.  bm_get_layout reports the layout each kind runs with
+ * (0 or 1).  Results differ between layouts only in the order of
+ * floating-point additions.  Errors: BM_ERR_INVALID for a value outside
+ * {-1, 0, 1}.
+ */
+bm_status bm_set_layout(bm_handle h, const int32_t* layout);
+bm_status bm_get_layout(bm_handle h, int32_t* layout);
+/*
+ * bm_gather_roof -- measurement aid for the roofline of the sparse passes
+ * (no counterpart in the paper).  Times a gather-only pass over the entries of
+ * pass kind `kind` in its index order (CSR kinds gather rows of H, CSC kinds
+ * rows of W, FP32, the handle's current row stride): every entry loads its
+ * whole row and nothing is computed or stored per entry.  *ms (nullable)
+ * receives the fastest of three launches after a warm-up, *gbs (nullable) the
+ * gathered bytes per second in GB/s.  A pass that gathers the same rows cannot
+ * run faster without reusing rows; the ratio of the two times is the pass's
+ * fraction of this roof.  Needs factors (k >= 1); allocates a small output
+ * buffer.  Errors: BM_ERR_INVALID for an unknown kind or no factors.
+ */
+bm_status bm_gather_roof(bm_handle h, int32_t kind, double* ms, double* gbs);
 
 /*
  * Batched BM phase over many solves.  A batch groups handles on one device

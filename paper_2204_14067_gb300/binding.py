@@ -55,7 +55,8 @@ PASS_NAMES = ("grad_csr", "grad_csc", "linesearch_csr", "spmm_csr", "spmm_csc")
 
 class bm_tune_info(ctypes.Structure):
     _fields_ = [("panels", ctypes.c_int32 * BM_PASS_KINDS), ("timed", ctypes.c_int32),
-                ("ms", ctypes.c_double * BM_PASS_KINDS), ("ms_single", ctypes.c_double * BM_PASS_KINDS)]
+                ("ms", ctypes.c_double * BM_PASS_KINDS), ("ms_single", ctypes.c_double * BM_PASS_KINDS),
+                ("layout", ctypes.c_int32 * BM_PASS_KINDS), ("pad_", ctypes.c_int32)]
 
 
 class bm_prox_info(ctypes.Structure):
@@ -104,6 +105,9 @@ _SIGS = {
     "bm_set_state": (_c.c_int, [_P, _P, _c.c_size_t]),
     "bm_set_panels": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_get_panels": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
+    "bm_set_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
+    "bm_gather_roof": (_c.c_int, [_P, _c.c_int32, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
+    "bm_get_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_profile_read": (_c.c_int, [_P, _c.c_int32, _P, _P, _P, _P]),
 }
 
@@ -300,11 +304,12 @@ def bm_solve(h, max_outer=100, tol=1e-10, F_target=0.0, time_limit_s=0.0, raise_
 
 
 def bm_autotune(h, max_panels=BM_MAX_PANELS):
-    """Time the sparse passes' work splits and keep the fastest; returns
-    {pass name: (panels, ms chosen, ms with one panel)}."""
+    """Time the sparse passes' work splits and kernel layouts and keep the
+    fastest; returns {pass name: (panels, ms chosen, ms with one panel and the
+    automatic layout, layout)}."""
     info = bm_tune_info()
     _check(lib().bm_autotune(h, int(max_panels), ctypes.byref(info)), h)
-    return {nm: (int(info.panels[i]), float(info.ms[i]), float(info.ms_single[i]))
+    return {nm: (int(info.panels[i]), float(info.ms[i]), float(info.ms_single[i]), int(info.layout[i]))
             for i, nm in enumerate(PASS_NAMES)}
 
 
@@ -330,6 +335,27 @@ def bm_set_panels(h, panels):
 def bm_get_panels(h):
     arr = (ctypes.c_int32 * BM_PASS_KINDS)()
     _check(lib().bm_get_panels(h, arr), h)
+    return [int(x) for x in arr]
+
+
+def bm_gather_roof(h, kind):
+    """(ms, GB/s) of a gather-only pass over pass kind `kind` (index into PASS_NAMES or its name)."""
+    if isinstance(kind, str):
+        kind = PASS_NAMES.index(kind)
+    ms, gbs = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bm_gather_roof(h, int(kind), ctypes.byref(ms), ctypes.byref(gbs)), h)
+    return ms.value, gbs.value
+
+
+def bm_set_layout(h, layout):
+    """Kernel layout per pass kind: -1 automatic, 0 lane group per segment, 1 warp per segment."""
+    arr = (ctypes.c_int32 * BM_PASS_KINDS)(*[int(x) for x in layout])
+    _check(lib().bm_set_layout(h, arr), h)
+
+
+def bm_get_layout(h):
+    arr = (ctypes.c_int32 * BM_PASS_KINDS)()
+    _check(lib().bm_get_layout(h, arr), h)
     return [int(x) for x in arr]
 
 

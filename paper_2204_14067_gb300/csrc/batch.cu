@@ -262,6 +262,7 @@ struct Group {  // problems that share a row width and gather type (one batched 
   DevBuf<PipeArgs> a_csr, a_csc, a_ls;
   DevBuf<int64_t> pre_csr, pre_csc, pre_ls;
   int64_t tot_csr = 0, tot_csc = 0, tot_ls = 0;
+  int64_t nnz = 0;                   // entries of the members (each pass visits all of them)
 };
 
 }  // namespace
@@ -321,6 +322,7 @@ void build_tables(bm_batch_ctx& b) {
       gr->bf = pbf;
     }
     gr->members.push_back(p);
+    gr->nnz += ix.nnz;
     for (int pass = 0; pass < 2; ++pass) {
       const Segs& sg = pass_segs(ix, pass == 0 ? kPassGradCsr : kPassGradCsc);
       if (!sg.nmulti) continue;
@@ -444,7 +446,8 @@ void enqueue_epoch(bm_batch_ctx& b) {
     BM_CHECK_LAUNCH();
   }
   for (auto& g : b.groups)
-    launch_direct_batch<0>(g->a_csr.get(), g->pre_csr.get(), (int)g->members.size(), g->tot_csr, g->nchunk, g->bf, st);
+    launch_direct_batch<0>(g->a_csr.get(), g->pre_csr.get(), (int)g->members.size(), g->tot_csr, g->nchunk, g->bf,
+                           long_segments(g->nnz, g->tot_csr), st);
   BM_CHECK_LAUNCH();
   if (b.nfix_csr) {
     k_fix_batch<<<grid_for_work(b.ftot_csr), 256, 0, st>>>(b.fix_csr.get(), b.fpre_csr.get(), b.nfix_csr);
@@ -453,7 +456,8 @@ void enqueue_epoch(bm_batch_ctx& b) {
   k_seg_sums_batch<<<b.count, 256, 0, st>>>(b.dense.get(), 0, b.scal.get());
   BM_CHECK_LAUNCH();
   for (auto& g : b.groups)
-    launch_direct_batch<0>(g->a_csc.get(), g->pre_csc.get(), (int)g->members.size(), g->tot_csc, g->nchunk, g->bf, st);
+    launch_direct_batch<0>(g->a_csc.get(), g->pre_csc.get(), (int)g->members.size(), g->tot_csc, g->nchunk, g->bf,
+                           long_segments(g->nnz, g->tot_csc), st);
   BM_CHECK_LAUNCH();
   if (b.nfix_csc) {
     k_fix_batch<<<grid_for_work(b.ftot_csc), 256, 0, st>>>(b.fix_csc.get(), b.fpre_csc.get(), b.nfix_csc);
@@ -470,7 +474,8 @@ void enqueue_epoch(bm_batch_ctx& b) {
     BM_CHECK_LAUNCH();
   }
   for (auto& g : b.groups)
-    launch_direct_batch<2>(g->a_ls.get(), g->pre_ls.get(), (int)g->members.size(), g->tot_ls, g->nchunk, g->bf, st);
+    launch_direct_batch<2>(g->a_ls.get(), g->pre_ls.get(), (int)g->members.size(), g->tot_ls, g->nchunk, g->bf,
+                           long_segments(g->nnz, g->tot_ls), st);
   BM_CHECK_LAUNCH();
   k_seg_sums_batch<<<b.count, 256, 0, st>>>(b.dense.get(), 1, b.scal.get());
   BM_CHECK_LAUNCH();

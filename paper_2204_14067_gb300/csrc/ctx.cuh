@@ -60,6 +60,10 @@ struct Index {
   // consecutive partial slots in entry order (same deterministic fix-up).
   std::map<int, std::unique_ptr<Segs>> rsp, csp;
   int panels[kPassKinds] = {1, 1, 1, 1, 1};   // panel count used by each pass kind
+  // Kernel layout of each pass kind: -1 automatic (warp per segment when the
+  // segments hold >= 512 entries on average, else a lane group per segment),
+  // 0 group per segment, 1 warp per segment (set by bm_autotune).
+  int layout[kPassKinds] = {-1, -1, -1, -1, -1};
 };
 
 // The work split a pass kind uses (the natural one when its panel count is 1).
@@ -72,6 +76,13 @@ inline const Segs& pass_segs(const Index& ix, int kind) {
     if (it != mp.end()) return *it->second;
   }
   return csr ? ix.rs : ix.cs;
+}
+
+// Whether a pass kind runs warp-per-segment (see Index::layout).
+inline bool pass_ws(const Index& ix, int kind) {
+  if (ix.layout[kind] >= 0) return ix.layout[kind] == 1;
+  const Segs& sg = pass_segs(ix, kind);
+  return sg.nseg > 0 && ix.nnz >= 512 * sg.nseg;
 }
 
 // Scratch reused across calls (sized once for the handle's k_max).

@@ -882,7 +882,8 @@ void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall&
     // The residual products of the PG step gather FP32 rows: BF16 operands
     // leave LmSVD short of its stop tolerance (the factor gathers of the BM
     // phase are the ones that use BF16).
-    BM_LAUNCH(h, csr ? "spmm_csr" : "spmm_csc", launch_pipe<1>(a, h.stream, false));
+    BM_LAUNCH(h, csr ? "spmm_csr" : "spmm_csc",
+              launch_pipe<1>(a, h.stream, false, pass_ws(ix, csr ? kPassSpmmCsr : kPassSpmmCsc)));
     if (sg.nmulti) {
       BM_LAUNCH(h, "spmm_fixup",
                 k_spmm_fixup<<<grid1(sg.nmulti * cols), 256, 0, h.stream>>>(

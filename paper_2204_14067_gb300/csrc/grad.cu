@@ -136,7 +136,7 @@ void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
     a.ldb = h.ldb;
   }
   BM_LAUNCH(h, csr ? (bf ? "grad_csr_bf16" : "grad_csr") : (bf ? "grad_csc_bf16" : "grad_csc"),
-            launch_pipe<0>(a, h.stream, bf));
+            launch_pipe<0>(a, h.stream, bf, pass_ws(ix, csr ? kPassGradCsr : kPassGradCsc)));
   if (sg.nmulti) {
     const int64_t work = sg.nmulti * h.ld;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), num_sms() * 8));
@@ -269,7 +269,7 @@ int64_t ls_pass(bm_ctx& h) {
     a.g1b = h.DHb.get();
     a.ldb = h.ldb;
   }
-  BM_LAUNCH(h, bf ? "linesearch_csr_bf16" : "linesearch_csr", launch_pipe<2>(a, h.stream, bf));
+  BM_LAUNCH(h, bf ? "linesearch_csr_bf16" : "linesearch_csr", launch_pipe<2>(a, h.stream, bf, pass_ws(ix, kPassLsCsr)));
   return sg.nseg;
 }
 }  // namespace

@@ -320,9 +320,13 @@ __global__ void k_panel_bounds(const int64_t* __restrict__ ptr, const int32_t* _
 }
 
 // Segments of at most kSegNnz entries within each (row, panel) piece,
-// emitted panel by panel, rows in order within a panel.  A row with no
-// entries gets one empty segment (its output is written all the same); a row
-// with several segments owns consecutive partial slots in entry order.
+// emitted panel by panel.  A row with no entries gets one empty segment (its
+// output is written all the same); a row with several segments owns
+// consecutive partial slots in entry order.  Within a panel the segments are
+// ordered by decreasing length (ties in row order), so that the lane groups
+// of one warp, which take consecutive segments, walk about as many entries
+// each; the order changes no result (every segment's sums and slots are its
+// own).
 void build_segs_from_bounds(Segs& s, const std::vector<int64_t>& bnd, int64_t rows, int P, cudaStream_t st) {
   const int W = P + 1;
   std::vector<int32_t> cnt(rows), first(rows, -1), used(rows, 0);
@@ -343,6 +347,7 @@ void build_segs_from_bounds(Segs& s, const std::vector<int64_t>& bnd, int64_t ro
   }
   BM_REQUIRE(nslots < ((int64_t)1 << 31), BM_ERR_INVALID, "index: too many partial slots");
   for (int p = 0; p < P; ++p) {
+    const size_t first_seg = srow.size();
     for (int64_t i = 0; i < rows; ++i) {
       const int64_t b = bnd[i * W + p], e = bnd[i * W + p + 1];
       if (b == e) {
@@ -361,6 +366,24 @@ void build_segs_from_bounds(Segs& s, const std::vector<int64_t>& bnd, int64_t ro
         sslot.push_back(cnt[i] > 1 ? first[i] + used[i]++ : -1);
       }
     }
+    // this panel's segments by decreasing length
+    const size_t cnt_p = srow.size() - first_seg;
+    std::vector<size_t> ord(cnt_p);
+    for (size_t q = 0; q < cnt_p; ++q) ord[q] = first_seg + q;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](size_t x, size_t y) { return send[x] - sbeg[x] > send[y] - sbeg[y]; });
+    std::vector<int32_t> r2(cnt_p), sl2(cnt_p);
+    std::vector<int64_t> b2(cnt_p), e2(cnt_p);
+    for (size_t q = 0; q < cnt_p; ++q) {
+      r2[q] = srow[ord[q]];
+      b2[q] = sbeg[ord[q]];
+      e2[q] = send[ord[q]];
+      sl2[q] = sslot[ord[q]];
+    }
+    std::copy(r2.begin(), r2.end(), srow.begin() + first_seg);
+    std::copy(b2.begin(), b2.end(), sbeg.begin() + first_seg);
+    std::copy(e2.begin(), e2.end(), send.begin() + first_seg);
+    std::copy(sl2.begin(), sl2.end(), sslot.begin() + first_seg);
   }
   s.nseg = (int64_t)srow.size();
   s.nmulti = (int64_t)mrow.size();

@@ -230,6 +230,8 @@ def named_config(name: str, **kw) -> Problem:
     tiny     : 500 x 300 planted rank 5, 10% uniform, lambda 0.5, k0 = 8
     tiny5    : same matrix, lambda 5 (planted-rank recovery case)
     netflix  : 480,189 x 17,770, 100,480,507 Zipf(1.2) ratings 1..5, k <= 64
+    netflix_quarter : 120,047 x 17,770, 25,120,127 ratings, the same recipe (a
+               quarter of the users and entries: profiling captures)
     yahoo    : 1,000,990 x 624,961, 252,800,275 ratings 0..100, k <= 128
     small    : a scaled netflix-shaped case for parity runs (kw: m, n, nnz)
     """
@@ -239,6 +241,9 @@ def named_config(name: str, **kw) -> Problem:
         return planted_uniform(seed=0, lam=5.0, name=name, **kw)
     if name == "netflix":
         return zipf_ratings(480_189, 17_770, 100_480_507, rank=20, mean=3.6, sd=1.0, lo=1, hi=5,
+                            k_max=64, seed=1, name=name, **kw)
+    if name == "netflix_quarter":
+        return zipf_ratings(120_047, 17_770, 25_120_127, rank=20, mean=3.6, sd=1.0, lo=1, hi=5,
                             k_max=64, seed=1, name=name, **kw)
     if name == "yahoo":
         return zipf_ratings(1_000_990, 624_961, 252_800_275, rank=32, mean=50.0, sd=20.0, lo=0,

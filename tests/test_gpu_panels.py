@@ -138,10 +138,11 @@ def test_autotune_keeps_results(B, prob):
         B.bm_init(h)
         res = B.bm_autotune(h)
         assert set(res) == set(B.binding.PASS_NAMES)
-        for nm, (P, ms, ms1) in res.items():
-            assert 1 <= P <= B.binding.BM_MAX_PANELS and ms > 0 and ms1 > 0
-            assert ms <= ms1 or P == 1
+        for nm, (P, ms, ms1, lay) in res.items():
+            assert 1 <= P <= B.binding.BM_MAX_PANELS and ms > 0 and ms1 > 0 and lay in (0, 1)
+            assert ms <= ms1 or (P == 1 and lay == B.bm_get_layout(h)[B.binding.PASS_NAMES.index(nm)])
         assert B.bm_get_panels(h) == [res[nm][0] for nm in B.binding.PASS_NAMES]
+        assert B.bm_get_layout(h) == [res[nm][3] for nm in B.binding.PASS_NAMES]
         r = B.bm_solve(h, max_outer=5, tol=0.0)
         assert np.isfinite(r["F"])
     finally:
