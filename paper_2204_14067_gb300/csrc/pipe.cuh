@@ -164,6 +164,10 @@ __device__ __forceinline__ void group_segment(const PipeArgs& a, int64_t s) {
   const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
   const int fl = WS ? lane : l;              // this lane fetches entry t0 + fl
   const int nch = a.nchunk;
+  // factor rows (MODE 0, 2) of an exact width have a compile-time stride
+  constexpr int kW = 4 * L * V;
+  const int ld = (MODE != 1 && EX) ? kW : a.ld;
+  const int ldb = (MODE != 1 && EX && kW % 8 == 0) ? kW : a.ldb;
   const bool live = s >= 0;
   const int i = live ? a.seg_row[s] : 0;
   const int64_t beg = live ? a.seg_beg[s] : 0;
@@ -179,9 +183,9 @@ __device__ __forceinline__ void group_segment(const PipeArgs& a, int64_t s) {
   for (int v = 0; v < V; ++v) {
     const int c = l + L * v;
     const bool in = live && (EX || c < nch);
-    w[v] = (MODE != 1 && in) ? __ldg(reinterpret_cast<const float4*>(a.o0 + (int64_t)i * a.ld) + c)
+    w[v] = (MODE != 1 && in) ? __ldg(reinterpret_cast<const float4*>(a.o0 + (int64_t)i * ld) + c)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
-    dw[v] = (MODE == 2 && in) ? __ldg(reinterpret_cast<const float4*>(a.o1 + (int64_t)i * a.ld) + c)
+    dw[v] = (MODE == 2 && in) ? __ldg(reinterpret_cast<const float4*>(a.o1 + (int64_t)i * ld) + c)
                               : make_float4(0.f, 0.f, 0.f, 0.f);
     acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -204,7 +208,7 @@ __device__ __forceinline__ void group_segment(const PipeArgs& a, int64_t s) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int c = l + L * v;
-          hv[v] = (EX || c < nch) ? gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          hv[v] = (EX || c < nch) ? gather4<BF>(a.g0, a.g0b, jj, ld, ldb, c) : make_float4(0.f, 0.f, 0.f, 0.f);
           d = fmaf(w[v].x, hv[v].x, fmaf(w[v].y, hv[v].y, fmaf(w[v].z, hv[v].z, fmaf(w[v].w, hv[v].w, d))));
         }
 #pragma unroll
@@ -229,7 +233,7 @@ __device__ __forceinline__ void group_segment(const PipeArgs& a, int64_t s) {
         for (int v = 0; v < V; ++v) {
           const int c = l + L * v;
           if (EX || c < nch) {
-            const float4 x = gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c);
+            const float4 x = gather4<BF>(a.g0, a.g0b, jj, ld, ldb, c);
             acc[v].x = fmaf(vv, x.x, acc[v].x);
             acc[v].y = fmaf(vv, x.y, acc[v].y);
             acc[v].z = fmaf(vv, x.z, acc[v].z);
@@ -242,8 +246,8 @@ __device__ __forceinline__ void group_segment(const PipeArgs& a, int64_t s) {
         for (int v = 0; v < V; ++v) {
           const int c = l + L * v;
           if (EX || c < nch) {
-            const float4 h = gather4<BF>(a.g0, a.g0b, jj, a.ld, a.ldb, c);
-            const float4 dh = gather4<BF>(a.g1, a.g1b, jj, a.ld, a.ldb, c);
+            const float4 h = gather4<BF>(a.g0, a.g0b, jj, ld, ldb, c);
+            const float4 dh = gather4<BF>(a.g1, a.g1b, jj, ld, ldb, c);
             b = fmaf(dw[v].x, h.x, fmaf(dw[v].y, h.y, fmaf(dw[v].z, h.z, fmaf(dw[v].w, h.w, b))));
             b = fmaf(w[v].x, dh.x, fmaf(w[v].y, dh.y, fmaf(w[v].z, dh.z, fmaf(w[v].w, dh.w, b))));
             c2 = fmaf(dw[v].x, dh.x, fmaf(dw[v].y, dh.y, fmaf(dw[v].z, dh.z, fmaf(dw[v].w, dh.w, c2))));

@@ -1,16 +1,24 @@
 """BF16-gather precision mode (bm_options.precision = 1).
 
 The gathered factor rows are read as bfloat16 (8-bit mantissa); owned rows,
-accumulation and the residual stay FP32.  Measured errors against FP64 are
-bounded per result (loss, gradients); a solve in this mode refines its final
-iterations in FP32 and must reach the plain FP32 solve's objective within
-1e-4 relative.
+accumulation and the residual stay FP32.  Errors against FP64 measured at the
+recommendation-scale sizes (480,189 x 17,770 at k = 64 and 1,000,990 x
+624,961 at k = 127): loss 6e-9 and 3e-8 relative, gradient rows at most
+2.3e-3 relative (median 1.6e-3, the bfloat16 rounding 2^-9 of the gathered
+rows).  On this test's smaller problem (160,000 entries, errors average
+over fewer terms) a bfloat16 emulation of the gathers gives at most: loss
+2.8e-6, gradient 1.6e-3 (Frobenius), per-row ratio 2.1e-3 with the
+rounding-scale floor of tests/parity.py.  The bounds below are twice those
+figures.  A solve in this mode refines its
+final iterations in FP32 and must reach the plain FP32 solve's objective
+within 1e-4 relative.
 """
 import numpy as np
 import pytest
 
 from oracle import bm_oracle as O
 from synth import named_config, random_factors
+from tests.parity import assert_rows_close, grad_rounding_scales
 
 pytestmark = pytest.mark.gpu
 
@@ -39,13 +47,16 @@ def test_bf16_loss_grad_error_bounds(B, k):
         f, F = B.bm_loss_grad(h, gW, gH)
         ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
         Wi, Hi = (H, W) if ix.transposed else (W, H)
-        fo, Fo, gWo, gHo, _ = O.loss_grad(ix, Wi.astype(np.float64), Hi.astype(np.float64), p.lam)
+        fo, Fo, gWo, gHo, r = O.loss_grad(ix, Wi.astype(np.float64), Hi.astype(np.float64), p.lam)
+        aW, aH = grad_rounding_scales(ix, r, Wi, Hi, p.lam)
         if ix.transposed:
-            gWo, gHo = gHo, gWo
+            gWo, gHo, aW, aH = gHo, gWo, aH, aW
         # bfloat16 rounding of the gathered rows (relative 2^-9) enters every dot product
-        assert abs(f - fo) <= 1e-2 * fo
-        assert np.linalg.norm(gW - gWo) <= 1e-2 * np.linalg.norm(gWo)
-        assert np.linalg.norm(gH - gHo) <= 1e-2 * np.linalg.norm(gHo)
+        assert abs(f - fo) <= 6e-6 * fo
+        assert np.linalg.norm(gW - gWo) <= 3.2e-3 * np.linalg.norm(gWo)
+        assert np.linalg.norm(gH - gHo) <= 3.2e-3 * np.linalg.norm(gHo)
+        assert_rows_close(gW, gWo, 4.2e-3, what="gW (bf16 gathers)", extra=aW)
+        assert_rows_close(gH, gHo, 4.2e-3, what="gH (bf16 gathers)", extra=aH)
     finally:
         B.bm_destroy(h)
 
