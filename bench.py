@@ -174,6 +174,7 @@ def run_ours(args):
     opt = B.bm_default_options()
     opt.precision = args.precision
     opt.value_codec = args.codec
+    opt.tensor_grams = args.tensor_grams
     if args.lmsvd_tol is not None:
         opt.lmsvd_tol = args.lmsvd_tol
     k_cap = min(p.k_max, 127)            # the library's rank cap (k_max + 1 vectors fit 128-wide rows)
@@ -880,6 +881,7 @@ def run_bcd(args):
     for solver in ("pr_cg", "column_blocks"):
         opt = B.bm_default_options()
         opt.value_codec = args.codec
+        opt.tensor_grams = args.tensor_grams
         h = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, p.k_max, opt)
         stream = torch.cuda.Stream()
         B.bm_set_stream(h, stream)
@@ -950,6 +952,8 @@ def main():
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the natural work split (one panel)")
+    ap.add_argument("--tensor-grams", type=int, default=1, choices=[0, 1],
+                    help="plain Grams of the PG step on the tensor cores (1) or the FP32 pipes (0)")
     ap.add_argument("--no-extra", action="store_true",
                     help="grad mode: skip the secondary figures (cycle, time to oracle, serving sample)")
     args = ap.parse_args()

@@ -76,6 +76,12 @@ typedef struct {
   int32_t bm_solver;     /* BM phase of bm_solve: 0 Polak-Ribiere+ CG on all of (W, H) with
                             the exact line search; 1 column-block coordinate descent
                             (bm_bcd_phase); 0 */
+  int32_t tensor_grams;  /* 1: the PG step's plain Grams (W^T U, H^T Y and the Rayleigh-Ritz
+                            matrix of LmSVD) run on the tensor cores from bfloat16 slices
+                            (see bm_dense_gram, mode 2); the Grams that need compensated
+                            sums (orthonormalisation, B B^T, W^T W, H^T H) stay on the FP32
+                            pipes; 0: every Gram on the FP32 pipes; 1 */
+  int32_t pad_;
 } bm_options;
 
 /* Result of one inexact PG step (Eq. "inexactpg", "truncate"). */
@@ -297,6 +303,31 @@ bm_status bm_get_layout(bm_handle h, int32_t* layout);
  * buffer.  Errors: BM_ERR_INVALID for an unknown kind or no factors.
  */
 bm_status bm_gather_roof(bm_handle h, int32_t kind, double* ms, double* gbs);
+
+/*
+ * bm_dense_gram -- C = A^T B of two tall FP32 blocks, the dense k-wide
+ * product of the PG step (Eq. "PUi"/"orth-W" Grams; Algorithm 2's
+ * Rayleigh-Ritz matrix), exposed for callers and tests.
+ *   A      float[L * lda] device, row-major L x a (a columns used)
+ *   B      float[L * ldb] device, row-major L x b
+ *   C      double[a * b] device, row-major (written)
+ *   mode   0: FP32 pipes, FP32 sums over 32-row tiles added as FP32 pairs;
+ *          1: FP32 pipes, compensated (error-free products and sums, about
+ *             FP64 accuracy); 2: tensor cores (tcgen05.mma, kind::f16):
+ *             each value split into three bfloat16 slices, six slice
+ *             products per 16-row step accumulated in FP32 per block slab,
+ *             the slab sums added in FP64 -- about FP32 accuracy.
+ *   stream cudaStream_t (NULL: default stream); the call returns after it
+ *          has finished.  Scratch is allocated on first use and kept for
+ *          later calls, one set per host thread.
+ * Requirements: L >= 0, 1 <= a, b; lda, ldb multiples of 4 with lda >= a,
+ * ldb >= b; A, B 16-byte aligned; mode 2 also a, b <= 256.  Errors:
+ * BM_ERR_INVALID for bad arguments, BM_ERR_CUDA for a launch failure,
+ * BM_ERR_NUMERIC if a tensor-core wait ran out of time (C is then NaN).
+ */
+bm_status bm_dense_gram(const float* A, int64_t L, int32_t a, int32_t lda, const float* B, int32_t b, int32_t ldb,
+                        double* C, int32_t mode, void* stream);
+const char* bm_dense_last_error(void);
 
 /*
  * Batched BM phase over many solves.  A batch groups handles on one device

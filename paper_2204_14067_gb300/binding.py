@@ -35,7 +35,8 @@ class bm_options(ctypes.Structure):
                 ("lmsvd_tol", ctypes.c_double), ("tau", ctypes.c_double), ("ritz_rel", ctypes.c_double),
                 ("psi0", ctypes.c_double), ("k_init", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("autotune", ctypes.c_int32), ("step_rule", ctypes.c_int32),
-                ("value_codec", ctypes.c_int32), ("bm_solver", ctypes.c_int32)]
+                ("value_codec", ctypes.c_int32), ("bm_solver", ctypes.c_int32), ("tensor_grams", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class bm_bb_options(ctypes.Structure):
@@ -107,6 +108,9 @@ _SIGS = {
     "bm_get_panels": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_set_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_gather_roof": (_c.c_int, [_P, _c.c_int32, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
+    "bm_dense_gram": (_c.c_int, [_P, _c.c_int64, _c.c_int32, _c.c_int32, _P, _c.c_int32, _c.c_int32, _P, _c.c_int32,
+                                 _P]),
+    "bm_dense_last_error": (_c.c_char_p, []),
     "bm_get_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_profile_read": (_c.c_int, [_P, _c.c_int32, _P, _P, _P, _P]),
 }
@@ -345,6 +349,19 @@ def bm_gather_roof(h, kind):
     ms, gbs = ctypes.c_double(), ctypes.c_double()
     _check(lib().bm_gather_roof(h, int(kind), ctypes.byref(ms), ctypes.byref(gbs)), h)
     return ms.value, gbs.value
+
+
+def bm_dense_gram(A, B, C, mode, stream=None):
+    """C (a x b float64 CUDA tensor) = A^T B for CUDA float32 tensors A (L x lda), B (L x ldb) whose
+    leading a, b columns are used (a = C.shape[0], b = C.shape[1]); mode 0 FP32 pipes, 1 compensated,
+    2 tensor cores."""
+    raw = getattr(stream, "cuda_stream", stream)
+    a, b = int(C.shape[0]), int(C.shape[1])
+    st = lib().bm_dense_gram(_ptr(A), int(A.shape[0]), a, int(A.shape[1]), _ptr(B), b, int(B.shape[1]), _ptr(C),
+                             int(mode), raw)
+    if st != BM_OK:
+        msg = lib().bm_dense_last_error()
+        raise BMError(st, msg.decode() if msg else "")
 
 
 def bm_set_layout(h, layout):

@@ -287,6 +287,8 @@ bm_status bm_default_options(bm_options* o) {
   o->step_rule = 0;
   o->value_codec = 1;
   o->bm_solver = 0;
+  o->tensor_grams = 1;
+  o->pad_ = 0;
   o->seed = 0;
   return BM_OK;
 }
@@ -316,6 +318,7 @@ bm_status bm_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, cons
     BM_REQUIRE(o.step_rule == 0 || o.step_rule == 1, BM_ERR_INVALID, "bm_create: step_rule must be 0 or 1");
     BM_REQUIRE(o.value_codec == 0 || o.value_codec == 1, BM_ERR_INVALID, "bm_create: value_codec must be 0 or 1");
     BM_REQUIRE(o.bm_solver == 0 || o.bm_solver == 1, BM_ERR_INVALID, "bm_create: bm_solver must be 0 or 1");
+    BM_REQUIRE(o.tensor_grams == 0 || o.tensor_grams == 1, BM_ERR_INVALID, "bm_create: tensor_grams must be 0 or 1");
     BM_REQUIRE(o.lmsvd_imax >= 1 && o.k_init >= 1 && o.bm_epochs >= 0 && o.pg_steps >= 0, BM_ERR_INVALID,
                "bm_create: iteration counts out of range");
     h = new bm_ctx();

@@ -808,6 +808,8 @@ void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, 
     BM_CUDA(cudaMemsetAsync(C, 0, (size_t)a * b * sizeof(double), h.stream));
     return;
   }
+  // plain Grams on the tensor cores when the handle allows it and the shape fits
+  if (!compensated && h.opt.tensor_grams == 1 && gram_tc_dev(h, w, A, B, C, tag)) return;
   const int sym = (A.p == B.p && A.ld == B.ld && a == b) ? 1 : 0;
   const int ng = (a + 7) / 8, nb = (b + 3) / 4;
   const int tiles = ng * nb;
@@ -830,8 +832,12 @@ void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, 
     allow_max_smem((const void*)k_gram<false>);
     BM_LAUNCH(h, tag, k_gram<false><<<grid, threads, smem, h.stream>>>(A.p, A.ld, a, B.p, B.ld, b, L, slab, sym, part));
   }
+  gram_reduce_dev(h, part, (int)gx, a, b, sym, C);
+}
+
+void gram_reduce_dev(bm_ctx& h, const float2* part, int slabs, int a, int b, int sym, double* C) {
   BM_LAUNCH(h, "gram_reduce", k_gram_reduce<<<(unsigned)ceil_div((int64_t)a * b, 32), 256, 0, h.stream>>>(
-                                  part, (int)gx, a, b, sym, C));
+                                  part, slabs, a, b, sym, C));
 }
 
 void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, float beta, float gamma,

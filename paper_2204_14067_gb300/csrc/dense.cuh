@@ -19,6 +19,7 @@ struct Tall {
 struct DenseWork {
   DevBuf<double> gram_part;   // slab partials of Grams
   DevBuf<int> status;         // eigensolver status flags
+  DevBuf<int> tc_status;      // tensor-core Gram: 1 after a barrier wait ran out (results poisoned with NaN)
   DevBuf<double> scratch;     // eigensolver work matrices
 };
 
@@ -26,6 +27,16 @@ struct DenseWork {
 // compensated: FP32 two-product/two-sum within a row tile (near-exact sums).
 void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, bool compensated,
               const char* tag);
+
+// Tensor-core form of a plain Gram (gram_tc.cu): bfloat16 slices, six slice
+// products per row step on tcgen05.mma, FP32 accumulation per block slab,
+// FP64 sum of the slabs.  Returns false, launching nothing, when the shape
+// does not fit it (a or b > 256, unaligned rows or bases).
+bool gram_tc_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, const char* tag);
+
+// C (a x b FP64) = sum over `slabs` FP32-pair slab partials (slab-major,
+// a x b each, row-major), added in slab order; sym: read (j, i) for i > j.
+void gram_reduce_dev(bm_ctx& h, const float2* part, int slabs, int a, int b, int sym, double* C);
 
 // Y = beta * Y + gamma * A * C, A: L x a, C: a x b FP32 (row-major, ldc), Y: L x b.
 void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, float beta, float gamma,
