@@ -76,11 +76,13 @@ typedef struct {
   int32_t bm_solver;     /* BM phase of bm_solve: 0 Polak-Ribiere+ CG on all of (W, H) with
                             the exact line search; 1 column-block coordinate descent
                             (bm_bcd_phase); 0 */
-  int32_t tensor_grams;  /* 1: the PG step's plain Grams (W^T U, H^T Y and the Rayleigh-Ritz
-                            matrix of LmSVD) run on the tensor cores from bfloat16 slices
-                            (see bm_dense_gram, mode 2); the Grams that need compensated
-                            sums (orthonormalisation, B B^T, W^T W, H^T H) stay on the FP32
-                            pipes; 0: every Gram on the FP32 pipes; 1 */
+  int32_t tensor_grams;  /* 1: the PG step's symmetric plain Gram (the Rayleigh-Ritz matrix
+                            (Z^T Q)^T (Z^T Q) of LmSVD) runs on the tensor cores from
+                            bfloat16 slices (see bm_dense_gram, mode 2); the thin products
+                            W^T U, H^T Y (faster on the FP32 pipes at these widths) and the
+                            Grams that need compensated sums (orthonormalisation, B B^T,
+                            W^T W, H^T H) stay on the FP32 pipes; 0: every Gram on the FP32
+                            pipes; 1 */
   int32_t pad_;
 } bm_options;
 

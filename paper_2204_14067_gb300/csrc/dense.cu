@@ -808,9 +808,13 @@ void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, 
     BM_CUDA(cudaMemsetAsync(C, 0, (size_t)a * b * sizeof(double), h.stream));
     return;
   }
-  // plain Grams on the tensor cores when the handle allows it and the shape fits
-  if (!compensated && h.opt.tensor_grams == 1 && gram_tc_dev(h, w, A, B, C, tag)) return;
   const int sym = (A.p == B.p && A.ld == B.ld && a == b) ? 1 : 0;
+  // symmetric plain Grams (the Rayleigh-Ritz matrix) on the tensor cores when
+  // the handle allows it and the shape fits: measured 0.43 -> 0.26 ms at the
+  // recommendation-scale size; the thin non-symmetric products (W^T U, H^T Y)
+  // run faster on the FP32 pipes (0.18 against 0.31 ms: staging and slicing
+  // two operands dominate at these widths) and stay there
+  if (!compensated && sym && h.opt.tensor_grams == 1 && gram_tc_dev(h, w, A, B, C, tag)) return;
   const int ng = (a + 7) / 8, nb = (b + 3) / 4;
   const int tiles = ng * nb;
   const int gy = (tiles + kGramMaxThreads - 1) / kGramMaxThreads;
