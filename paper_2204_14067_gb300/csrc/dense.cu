@@ -341,9 +341,11 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
       const T Kc = (T)0.5 * beta * block_sum<T>(tid < L ? vv[tid] * pp[tid] : (T)0, red);
       if (tid < L) pp[tid] -= Kc * vv[tid];
       __syncthreads();
-      for (int idx = tid; idx < L * L; idx += nt) {
-        const int r = idx / L, c = idx - r * L;
-        A[(k + 1 + r) * n + (k + 1 + c)] -= vv[r] * pp[c] + pp[r] * vv[c];
+      // rank-2 update of the trailing block: a warp per row, lanes along it
+      for (int r = tid >> 5; r < L; r += nt >> 5) {
+        const T vr = vv[r], pr = pp[r];
+        T* Ar = A + (k + 1 + r) * n + (k + 1);
+        for (int c = tid & 31; c < L; c += 32) Ar[c] -= vr * pp[c] + pr * vv[c];
       }
     }
     __syncthreads();
@@ -580,29 +582,32 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __rest
         qq_[tid] = q;
       }
       __syncthreads();
-      // rows p, q of A
-      for (int idx = tid; idx < half * np; idx += nt) {
-        const int k = idx / np, col = idx - k * np;
+      // rows p, q of A: a warp per pair, lanes along the row
+      const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+      for (int k = warp; k < half; k += nwarp) {
         const T c = cs_[k], s = sn_[k];
         if (s == (T)0) continue;
         const int p = pp_[k], q = qq_[k];
-        const T ap = A[p * np + col], aq = A[q * np + col];
-        A[p * np + col] = c * ap - s * aq;
-        A[q * np + col] = s * ap + c * aq;
+        for (int col = lane; col < np; col += 32) {
+          const T ap = A[p * np + col], aq = A[q * np + col];
+          A[p * np + col] = c * ap - s * aq;
+          A[q * np + col] = s * ap + c * aq;
+        }
       }
       __syncthreads();
-      // columns p, q of A and V
-      for (int idx = tid; idx < half * np; idx += nt) {
-        const int k = idx / np, row = idx - k * np;
+      // columns p, q of A and V: a warp per pair, lanes down the column
+      for (int k = warp; k < half; k += nwarp) {
         const T c = cs_[k], s = sn_[k];
         if (s == (T)0) continue;
         const int p = pp_[k], q = qq_[k];
-        const T ap = A[row * np + p], aq = A[row * np + q];
-        A[row * np + p] = c * ap - s * aq;
-        A[row * np + q] = s * ap + c * aq;
-        const T vp = V[row * np + p], vq = V[row * np + q];
-        V[row * np + p] = c * vp - s * vq;
-        V[row * np + q] = s * vp + c * vq;
+        for (int row = lane; row < np; row += 32) {
+          const T ap = A[row * np + p], aq = A[row * np + q];
+          A[row * np + p] = c * ap - s * aq;
+          A[row * np + q] = s * ap + c * aq;
+          const T vp = V[row * np + p], vq = V[row * np + q];
+          V[row * np + p] = c * vp - s * vq;
+          V[row * np + q] = s * vp + c * vq;
+        }
       }
       __syncthreads();
     }
