@@ -243,23 +243,30 @@ def run_ours(args):
     Wh = np.ascontiguousarray(W0)
     Hh = np.ascontiguousarray(H0)
     e2e_steps = max(1, min(args.steps, 3))
-    state = B.bm_get_state(h) if args.mode == "cycle" else None
+    if args.mode == "cycle":
+        # pinned host buffers for the state, sized for the largest rank
+        state = torch.empty(B.bm_state_size(h) + (1 << 20), dtype=torch.uint8, pin_memory=True)
+        n_state = B.bm_get_state(h, state)
+    else:
+        Wh = torch.from_numpy(Wh).pin_memory()
+        Hh = torch.from_numpy(Hh).pin_memory()
+        gW = torch.empty_like(Wh).pin_memory()
+        gH = torch.empty_like(Hh).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2d = d2h = 0
     for _ in range(e2e_steps):
         if args.mode == "grad":
             B.bm_set_factors(h, k, Wh, Hh)
-            gW = np.empty_like(Wh)
-            gH = np.empty_like(Hh)
             B.bm_loss_grad(h, gW, gH)
-            h2d, d2h = Wh.nbytes + Hh.nbytes, gW.nbytes + gH.nbytes
+            h2d = (Wh.numel() + Hh.numel()) * 4
+            d2h = (gW.numel() + gH.numel()) * 4
         else:
-            B.bm_set_state(h, state)
+            B.bm_set_state(h, state, n_state)
             B.bm_solve(h, max_outer=1, tol=0.0)
-            h2d = len(state)
-            state = B.bm_get_state(h)
-            d2h = len(state)
+            h2d = n_state
+            n_state = B.bm_get_state(h, state)
+            d2h = n_state
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     # secondary figures of the default (gradient) run: cycles of Algorithm 1
@@ -288,10 +295,13 @@ def run_ours(args):
                                    "final_rel": t["config"]["final_rel"], "e2e_s": t["e2e"]["value"],
                                    "oracle_s": (t["cpu_baseline"] or {}).get("value")}
         sub.serve_count = 16
+        sub.serve_max_nnz = 1_000_000
         sv = run_serve(sub)
         extra["serving"] = {"metric": sv["metric"], "value": sv["value"], "unit": sv["unit"],
                             "workload": sv["config"]["workload"], "batched_bf16": sv["batched_bf16"],
-                            "one_at_a_time_fp32": sv["one_at_a_time_fp32"], "final_objective": sv["final_objective"]}
+                            "one_at_a_time_fp32": sv["one_at_a_time_fp32"], "final_objective": sv["final_objective"],
+                            "oracle_check": sv["oracle_check"],
+                            "saturation_solves_per_s": sv["saturation_solves_per_s"]}
 
     ms_step, total_units, value = replica_throughput(dist, ms / args.steps, p.nnz)
     e2e_val = _sumall(dist, float(p.nnz)) / _maxall(dist, e2e_s)
@@ -577,20 +587,29 @@ def run_tto(args):
 
 
 def run_serve(args):
-    """Continuous-batching serving on a bounded sample of the request stream:
-    capacity of one-at-a-time FP32 solves, then Poisson arrivals at 0.8 of it
-    served by the batched BF16 server and by the one-at-a-time FP32 server."""
+    """Continuous-batching serving on a prefix of the serving stream (m
+    log-U[1k, 200k], n log-U[500, 20k], density log-U[0.1 %, 2 %], nnz up to
+    --serve-max-nnz, planted rank 2..16): half the requests take lambda from the
+    stream's grid {0.02 .. 0.5} max|A| (these run into the rank cap of 32), half
+    from {3, 5, 8} max|A| (optimum below the cap: the solves converge).  First
+    the capacity of one-at-a-time FP32 solves, then Poisson arrivals at 0.8 of
+    it served by the batched BF16 server (FP32 refinement) and by the
+    one-at-a-time FP32 server.  Final objectives of solves that converged in
+    both are compared, and a sample of served solutions is re-evaluated and
+    compared with the optimum by the FP64 oracle."""
     import torch
 
     import paper_2204_14067_gb300 as B
     from synth import serving_requests
 
     count = args.serve_count
-    probs, _ = serving_requests(count=count, seed=4, max_nnz=1_000_000, k_max=32)
+    probs, _ = serving_requests(count=count, seed=4, max_nnz=args.serve_max_nnz or None, k_max=32,
+                                lam_grid2=(3.0, 5.0, 8.0), share2=0.5)
     torch.cuda.synchronize()
+    cap_outer = 60
 
     def serve(arrivals, **kw):
-        s = B.bm_server_create(max_outer=60, tol=1e-7, **kw)   # 60: the cycle cap of a solve
+        s = B.bm_server_create(max_outer=cap_outer, tol=1e-7, keep_factors=1, **kw)
         try:
             t0 = time.perf_counter()
             ids = []
@@ -603,47 +622,75 @@ def run_serve(args):
             wall = time.perf_counter() - t0
             res = {r["id"]: r for r in B.bm_server_results(s)}
             err = B.binding.lib().bm_server_last_error(s)
-            return [res[i] for i in ids], wall, (err.decode() if err else "")
+            out = [res[i] for i in ids]
+            facs = {}
+            for j, (i, q) in enumerate(zip(ids, probs)):
+                if out[j]["status"] == 0:
+                    facs[j] = B.bm_server_factors(s, i, q.m, q.n)
+            return out, wall, (err.decode() if err else ""), facs
         finally:
             B.bm_server_destroy(s)
 
-    plain0, t_cap, _ = serve(np.zeros(count), max_active=1, precision=0, batched=0, workers=1)
+    plain0, t_cap, _, _ = serve(np.zeros(count), max_active=1, precision=0, batched=0, workers=1)
     cap = count / t_cap
+    # saturation throughput of the batched server (every request queued at 0)
+    bat0, t_cap_b, _, _ = serve(np.zeros(count), max_active=16, precision=1, batched=1, workers=8)
     rate = 0.8 * cap
     rng = np.random.default_rng(123)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
-    bat, wall_b, err_b = serve(arrivals, max_active=16, precision=1, batched=1, workers=8)
-    pla, wall_p, err_p = serve(arrivals, max_active=1, precision=0, batched=0, workers=1)
+    bat, wall_b, err_b, fb = serve(arrivals, max_active=16, precision=1, batched=1, workers=8)
+    pla, wall_p, err_p, fp = serve(arrivals, max_active=1, precision=0, batched=0, workers=1)
 
     def stats(res, wall):
         lat = np.array([r["t_done"] - r["t_submit"] for r in res])
         return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                "solves_per_s": len(res) / wall, "errors": int(sum(r["status"] != 0 for r in res))}
+                "solves_per_s": len(res) / wall, "wall_s": wall,
+                "errors": int(sum(r["status"] != 0 for r in res))}
 
     sb, sp = stats(bat, wall_b), stats(pla, wall_p)
     if err_b:
         sb["last_error"] = err_b
     if err_p:
         sp["last_error"] = err_p
-    # equal final objective: compared where both solves ended on the tolerance
-    # (a solve that ran into the cycle cap of 60 stopped wherever it was)
-    cap_outer = 60
-    ok = [(a, b) for a, b in zip(bat, pla) if a["status"] == 0 and b["status"] == 0]
-    conv = [(a, b) for a, b in ok if a["outer"] < cap_outer and b["outer"] < cap_outer]
-    rel_conv = max((abs(a["F"] - b["F"]) / abs(b["F"]) for a, b in conv), default=None)
-    rel_all = max((abs(a["F"] - b["F"]) / abs(b["F"]) for a, b in ok), default=None)
-    objective = {"converged_in_both": len(conv), "max_rel_diff_converged": rel_conv,
-                 "max_rel_diff_all": rel_all,
-                 "hit_cycle_cap": {"batched_bf16": int(sum(a["outer"] >= cap_outer for a, _ in ok)),
-                                   "one_at_a_time_fp32": int(sum(b["outer"] >= cap_outer for _, b in ok))}}
+    # equal final objective where both solves ended on the tolerance (a solve
+    # that ran into the cycle cap stopped wherever it was)
+    ok = [(j, a, b) for j, (a, b) in enumerate(zip(bat, pla)) if a["status"] == 0 and b["status"] == 0]
+    conv = [(j, a, b) for j, a, b in ok if a["outer"] < cap_outer and b["outer"] < cap_outer]
+    rel_conv = max((abs(a["F"] - b["F"]) / abs(b["F"]) for _, a, b in conv), default=None)
+    objective = {"converged_in_both": len(conv),
+                 "max_rel_diff_converged": rel_conv,
+                 "hit_cycle_cap": {"batched_bf16": int(sum(a["outer"] >= cap_outer for _, a, _ in ok)),
+                                   "one_at_a_time_fp32": int(sum(b["outer"] >= cap_outer for _, _, b in ok))}}
+    # the oracle on a sample: the smallest converged requests
+    check = None
+    if not args.no_cpu and conv:
+        from oracle import bm_oracle as O
+        sample = sorted(conv, key=lambda t: probs[t[0]].rows.shape[0])[:3]
+        rows_out = []
+        for j, a, b in sample:
+            q = probs[j]
+            ix = O.build_index(q.m, q.n, q.rows, q.cols, q.vals.astype(np.float64))
+            st, oi = O.solve(ix, q.lam, 8, q.k_max, O.Options(), max_outer=400, tol=1e-12)
+            F_star = oi.F_hist[-1]
+            ent = {"nnz": int(q.rows.shape[0]), "F_oracle_optimum": F_star}
+            for tag, fac in (("batched_bf16", fb.get(j)), ("one_at_a_time_fp32", fp.get(j))):
+                if fac is None:
+                    continue
+                W64, H64 = fac[0].astype(np.float64), fac[1].astype(np.float64)
+                Wi, Hi = (H64, W64) if ix.transposed else (W64, H64)
+                ent[tag + "_rel_to_optimum"] = (O.objective(ix, Wi, Hi, q.lam) - F_star) / F_star
+            rows_out.append(ent)
+        check = rows_out
     return {
         "metric": "serving solves/s (batched BF16 + FP32 refinement)", "value": sb["solves_per_s"],
         "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall_b * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
-        "config": {"workload": f"{count} requests: m log-U[1k,200k], n log-U[500,20k], density log-U[0.1%,2%], "
-                               "nnz <= 1M, planted rank 2..16, lambda {0.02..0.5} max|A|, k_max 32",
-                   "arrival_rate_per_s": rate, "fp32_capacity_per_s": cap},
-        "batched_bf16": sb, "one_at_a_time_fp32": sp, "final_objective": objective,
+        "config": {"workload": f"first {count} requests of the serving stream: m log-U[1k,200k], n log-U[500,20k], "
+                               f"density log-U[0.1%,2%], nnz <= {args.serve_max_nnz or 'density*m*n'}, planted rank "
+                               "2..16, lambda {0.02..0.5} max|A| or (half the requests) {3,5,8} max|A|, k_max 32",
+                   "arrival_rate_per_s": rate, "fp32_capacity_per_s": cap, "cycle_cap": cap_outer},
+        "batched_bf16": sb, "one_at_a_time_fp32": sp, "final_objective": objective, "oracle_check": check,
+        "saturation_solves_per_s": {"batched_bf16": count / t_cap_b, "one_at_a_time_fp32": cap},
     }
 
 
@@ -942,6 +989,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="1: BF16 copies of the gathered factor rows (cycle and grad modes)")
     ap.add_argument("--serve-count", type=int, default=24)
+    ap.add_argument("--serve-max-nnz", type=int, default=1_000_000,
+                    help="cap on a serving request's entries (0: none, the stream's own sizes up to about 80M)")
     ap.add_argument("--k", type=int, default=0, help="factor rank (default 64; at most the workload's cap)")
     ap.add_argument("--lmsvd-tol", type=float, default=None,
                     help="LmSVD stop tolerance (cycle and tto modes; default: the library's)")

@@ -317,8 +317,21 @@ def bm_autotune(h, max_panels=BM_MAX_PANELS):
             for i, nm in enumerate(PASS_NAMES)}
 
 
-def bm_get_state(h) -> bytes:
-    """Checkpoint of the solve state (host bytes)."""
+def bm_state_size(h) -> int:
+    """Bytes of the solve-state checkpoint."""
+    n = ctypes.c_size_t(0)
+    _check(lib().bm_get_state(h, None, ctypes.byref(n)), h)
+    return n.value
+
+
+def bm_get_state(h, out=None):
+    """Checkpoint of the solve state.  Without `out`: host bytes.  With `out`
+    (a contiguous host numpy uint8 array or CPU torch tensor, e.g. pinned, of
+    at least bm_state_size bytes): written in place, returns the byte count."""
+    if out is not None:
+        n = ctypes.c_size_t(int(out.nbytes) if hasattr(out, "nbytes") else out.numel() * out.element_size())
+        _check(lib().bm_get_state(h, _ptr(out), ctypes.byref(n)), h)
+        return n.value
     n = ctypes.c_size_t(0)
     _check(lib().bm_get_state(h, None, ctypes.byref(n)), h)
     buf = ctypes.create_string_buffer(n.value)
@@ -326,9 +339,16 @@ def bm_get_state(h) -> bytes:
     return buf.raw[: n.value]
 
 
-def bm_set_state(h, state: bytes):
-    buf = ctypes.create_string_buffer(bytes(state), len(state))
-    _check(lib().bm_set_state(h, buf, len(state)), h)
+def bm_set_state(h, state, nbytes=None):
+    """Restore a checkpoint: bytes, or a host numpy uint8 array / CPU torch
+    tensor (read in place; nbytes = the state's length when the buffer is larger)."""
+    if isinstance(state, (bytes, bytearray)):
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        _check(lib().bm_set_state(h, buf, len(state)), h)
+        return
+    n = int(nbytes) if nbytes is not None else (int(state.nbytes) if hasattr(state, "nbytes")
+                                                 else state.numel() * state.element_size())
+    _check(lib().bm_set_state(h, _ptr(state), n), h)
 
 
 def bm_set_panels(h, panels):

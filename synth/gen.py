@@ -336,12 +336,14 @@ def self_avoiding_chain(n=30_000, cutoff=6.0, noise=0.10, exclusion=1.0, seed=3,
 
 def serving_requests(count=2000, seed=4, m_range=(1_000, 200_000), n_range=(500, 20_000),
                      density_range=(0.001, 0.02), rank_range=(2, 16), lam_grid=(0.02, 0.05, 0.1, 0.2, 0.5),
-                     rate=None, k_max=32, max_nnz=None):
+                     rate=None, k_max=32, max_nnz=None, lam_grid2=None, share2=0.5):
     """A stream of completion requests: m, n and the density log-uniform in
     their ranges, nnz = density*m*n (capped at max_nnz), planted rank uniform
     in rank_range, ratings as in the recommendation workload, lambda = a grid
-    value times max|A|; arrival times from a Poisson process of the given
-    rate (requests per second; None: all at 0).  Returns (problems, arrivals)."""
+    value times max|A|; with lam_grid2, a share `share2` of the requests
+    (chosen by a separate draw) takes its lambda from lam_grid2 instead;
+    arrival times from a Poisson process of the given rate (requests per
+    second; None: all at 0).  Returns (problems, arrivals)."""
     rng = _rng(seed, 5)
     lu = lambda lo, hi, size: np.exp(rng.uniform(np.log(lo), np.log(hi), size))
     ms = np.round(lu(*m_range, count)).astype(np.int64)
@@ -349,6 +351,10 @@ def serving_requests(count=2000, seed=4, m_range=(1_000, 200_000), n_range=(500,
     ds = lu(*density_range, count)
     ranks = rng.integers(rank_range[0], rank_range[1] + 1, count)
     lams = rng.choice(np.asarray(lam_grid), count)
+    if lam_grid2 is not None:
+        rng2 = _rng(seed, 6)
+        pick = rng2.uniform(size=count) < share2
+        lams = np.where(pick, rng2.choice(np.asarray(lam_grid2), count), lams)
     probs = []
     for t in range(count):
         m, n = int(ms[t]), int(ns[t])

@@ -55,3 +55,27 @@ def test_state_rejects_damaged_or_foreign(B):
     finally:
         B.bm_destroy(a)
         B.bm_destroy(c)
+
+
+def test_state_through_caller_buffers(B):
+    """The state written into a caller's (pinned) buffer equals the bytes form
+    and restores the same solve as the bytes form does."""
+    torch = pytest.importorskip("torch")
+    p = named_config("small", m=3000, n=800, nnz=120_000, seed=73)
+    a = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 32)
+    b = B.bm_create(p.m, p.n, p.rows, p.cols, p.vals, p.lam, 32)
+    try:
+        B.bm_solve(a, max_outer=3, tol=0.0)
+        ref = B.bm_get_state(a)
+        buf = torch.zeros(B.bm_state_size(a) + 4096, dtype=torch.uint8).pin_memory()
+        n = B.bm_get_state(a, buf)
+        assert n == len(ref) and bytes(buf[:n].numpy().tobytes()) == ref
+        with pytest.raises(B.BMError):
+            B.bm_get_state(a, np.zeros(n - 1, np.uint8))      # too small
+        B.bm_set_state(b, buf, n)
+        ra = B.bm_solve(a, max_outer=2, tol=0.0)
+        rb = B.bm_solve(b, max_outer=2, tol=0.0)
+        assert ra["F"] == rb["F"] and ra["k"] == rb["k"]
+    finally:
+        B.bm_destroy(a)
+        B.bm_destroy(b)
