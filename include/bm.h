@@ -332,6 +332,28 @@ bm_status bm_dense_gram(const float* A, int64_t L, int32_t a, int32_t lda, const
 const char* bm_dense_last_error(void);
 
 /*
+ * bm_sym_eig -- eigen-decomposition S = V diag(evals) V^T of a small
+ * symmetric matrix on one thread block, the q x q eigenproblems of the PG
+ * step (Algorithm 2's Rayleigh-Ritz matrix Q^T L Q, the Gram B B^T of the
+ * exact small SVD, Eq. "orth-W"), exposed for callers and tests.
+ *   S      double[n * n] device, row-major; (S + S^T) / 2 is used
+ *   evals  double[n] device (written), descending
+ *   evecs  double[n * n] device (written), row-major, column j = vector j
+ *   mode   0: FP32 Householder tridiagonalisation + implicit QL (eigenvalue
+ *             errors about eps32 * ||S||); 1: mode 0's vectors V, then
+ *             S' = V^T S V in FP64 and FP32 Jacobi sweeps on S' to a
+ *             relative threshold (eigenvalues of a positive definite S to
+ *             about eps32 relative), for n <= 160; 2: as 1 with FP64 sweeps,
+ *             for n <= 112.  Modes 1 and 2 beyond those sizes run the
+ *             Householder + QL of mode 0 in FP64.
+ *   stream cudaStream_t (NULL: default stream); returns after it finished.
+ * Requirements: 1 <= n <= 256.  Errors: BM_ERR_INVALID for bad arguments,
+ * BM_ERR_NUMERIC for a non-finite eigenvalue or a QL that did not converge,
+ * BM_ERR_CUDA for a launch failure.
+ */
+bm_status bm_sym_eig(const double* S, int32_t n, double* evals, double* evecs, int32_t mode, void* stream);
+
+/*
  * Batched BM phase over many solves.  A batch groups handles on one device
  * (same precision mode, each with rank >= 1).  bm_batch_bm_phase runs
  * `epochs` iterations of the BM-phase solver of bm_bm_phase on every handle

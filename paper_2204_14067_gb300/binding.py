@@ -111,6 +111,7 @@ _SIGS = {
     "bm_dense_gram": (_c.c_int, [_P, _c.c_int64, _c.c_int32, _c.c_int32, _P, _c.c_int32, _c.c_int32, _P, _c.c_int32,
                                  _P]),
     "bm_dense_last_error": (_c.c_char_p, []),
+    "bm_sym_eig": (_c.c_int, [_P, _c.c_int32, _P, _P, _c.c_int32, _P]),
     "bm_get_layout": (_c.c_int, [_P, _c.POINTER(_c.c_int32)]),
     "bm_profile_read": (_c.c_int, [_P, _c.c_int32, _P, _P, _P, _P]),
 }
@@ -379,6 +380,16 @@ def bm_dense_gram(A, B, C, mode, stream=None):
     a, b = int(C.shape[0]), int(C.shape[1])
     st = lib().bm_dense_gram(_ptr(A), int(A.shape[0]), a, int(A.shape[1]), _ptr(B), b, int(B.shape[1]), _ptr(C),
                              int(mode), raw)
+    if st != BM_OK:
+        msg = lib().bm_dense_last_error()
+        raise BMError(st, msg.decode() if msg else "")
+
+
+def bm_sym_eig(S, evals, evecs, mode, stream=None):
+    """evals (n float64 CUDA tensor, descending) and evecs (n x n, column j = vector j) of the symmetric
+    n x n float64 CUDA tensor S; mode 0 FP32 QL, 1 with relative FP32 Jacobi refinement, 2 FP64 refinement."""
+    raw = getattr(stream, "cuda_stream", stream)
+    st = lib().bm_sym_eig(_ptr(S), int(S.shape[0]), _ptr(evals), _ptr(evecs), int(mode), raw)
     if st != BM_OK:
         msg = lib().bm_dense_last_error()
         raise BMError(st, msg.decode() if msg else "")

