@@ -339,9 +339,12 @@ const char* bm_dense_last_error(void);
  *   S      double[n * n] device, row-major; (S + S^T) / 2 is used
  *   evals  double[n] device (written), descending
  *   evecs  double[n * n] device (written), row-major, column j = vector j
- *   mode   0: FP32 Householder tridiagonalisation + implicit QL (eigenvalue
- *             errors about eps32 * ||S||); 1: mode 0's vectors V, then
- *             S' = V^T S V in FP64 and FP32 Jacobi sweeps on S' to a
+ *   mode   0: FP32 Householder tridiagonalisation + implicit QL, with one
+ *             divide-and-conquer level (QL on the two halves, merge through
+ *             the secular equation) for 24 <= n <= 150 (eigenvalue errors
+ *             about eps32 * ||S||); 1: mode 0's vectors made orthogonal by
+ *             one FP64 Newton-Schulz step (V), then S' = V^T S V in FP64 and
+ *             FP32 Jacobi sweeps on S' to a
  *             relative threshold (eigenvalues of a positive definite S to
  *             about eps32 relative), for n <= 160; 2: as 1 with FP64 sweeps,
  *             for n <= 112.  Modes 1 and 2 beyond those sizes run the

@@ -535,6 +535,500 @@ __global__ void __launch_bounds__(kEigThreads) k_sym_eig(const double* __restric
 }
 
 
+// One-CTA FP32 symmetric eigensolver with one divide-and-conquer level on the
+// tridiagonal matrix: T = diag(T1, T2) + beta v v^T (Cuppen), the two halves
+// by implicit QL at the same time (warps 0 and 1 generate the rotations, the
+// other warps apply them), then the rank-one merge: deflation of negligible
+// components and close poles, the secular equation by bisection from the
+// nearer pole, the eigenvector components recomputed from the computed roots
+// (Gu & Eisenstat, SIAM J. Matrix Anal. Appl. 16 (1995)), and the merged
+// vectors as one product.
+constexpr int kDcMin = 24;
+constexpr int kDcMax = 150;   // A and Z (n rows of dc_ld(n) floats each) in shared memory
+
+// Row stride of A and Z: at least n + 1, and 4 modulo 32, so that the eight
+// rows a warp reads four consecutive columns of (four threads to a row) fall
+// in 32 different shared-memory banks.
+__host__ __device__ constexpr int dc_ld(int n) { return ((n + 1 + 27) / 32) * 32 + 4; }
+
+__device__ __forceinline__ void ql_sweep_chain(float* d, float* e, int l, int m, float* cs, float* sn, int& cnt) {
+  float g = (d[l + 1] - d[l]) / (2.f * e[l]);
+  float r = sqrtf(g * g + 1.f);
+  g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+  float s = 1, c = 1, p = 0;
+  bool early = false;
+  float ei = e[m - 1], di = d[m - 1], dn = d[m];
+  cnt = 0;
+  for (int i = m - 1; i >= l; --i) {
+    const float ei_next = i > l ? e[i - 1] : 0.f, di_next = i > l ? d[i - 1] : 0.f;
+    const float f = s * ei, b = c * ei;
+    const float t2 = fmaf(f, f, g * g);
+    if (!(t2 > 1e-30f)) {
+      e[i + 1] = 0.f;
+      d[i + 1] = dn - p;
+      e[m] = 0.f;
+      early = true;
+      break;
+    }
+    const float y0 = rsqrtf(t2);
+    const float h = fmaf(-0.5f * t2, y0 * y0, 1.5f);
+    r = (t2 * y0) * h;
+    s = (f * y0) * h;
+    c = (g * y0) * h;
+    e[i + 1] = r;
+    g = dn - p;
+    r = fmaf(di - g, s, 2.f * b * c);
+    p = s * r;
+    d[i + 1] = g + p;
+    g = fmaf(c, r, -b);
+    cs[cnt] = c;
+    sn[cnt] = s;
+    ++cnt;
+    ei = ei_next;
+    dn = di;
+    di = di_next;
+  }
+  if (!early) {
+    d[l] -= p;
+    e[l] = g;
+    e[m] = 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(kEigThreads) k_sym_eig_dc(const double* __restrict__ S, int n,
+                                                            double* __restrict__ evals, double* __restrict__ evecs,
+                                                            float* __restrict__ gW, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char eig_raw[];
+  __shared__ float d[kEigMax], e[kEigMax], vv[kEigMax], pp[kEigMax], bet[kEigMax];
+  __shared__ float rc[2][2][kEigMax], rs[2][2][kEigMax];
+  __shared__ int rm[2][2], rcnt[2][2];
+  __shared__ float red[32];
+  __shared__ int sh_state, sh_done[2], sh_K, sh_nrot;
+  __shared__ float sh_anorm, sh_beta;
+  // merge: sorted poles and components, roots, recomputed components
+  __shared__ float ds[kDcMax], zs[kDcMax], dk[kDcMax], zk[kDcMax], tau[kDcMax], zhat[kDcMax], lam[kDcMax];
+  __shared__ int perm[kDcMax], kidx[kDcMax], org[kDcMax], kslot[kDcMax];
+  __shared__ int rot_a[kDcMax], rot_b[kDcMax];
+  __shared__ float rot_c[kDcMax], rot_s[kDcMax];
+  const int lda = dc_ld(n), ldz = lda;
+  float* A = reinterpret_cast<float*>(eig_raw);
+  float* Z = A + (size_t)n * lda;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const float eps = FLT_EPSILON;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx - i * n;
+    A[i * lda + j] = (float)(0.5 * (S[i * n + j] + S[j * n + i]));
+  }
+  __syncthreads();
+  // ---- tridiagonalisation (Golub & Van Loan, Sec. 8.3.1), four threads to a row
+  for (int k = 0; k + 2 < n; ++k) {
+    const int L = n - k - 1;
+    float x = tid < L ? A[(k + 1 + tid) * lda + k] : 0.f;
+    const float ss = block_sum<float>(x * x, red);
+    const float x0 = A[(k + 1) * lda + k];
+    const float alpha = ss > 0 ? (x0 > 0 ? -sqrtf(ss) : sqrtf(ss)) : 0.f;
+    const float v0 = x0 - alpha;
+    const float vtv = ss - x0 * x0 + v0 * v0;
+    const float beta = vtv > 0 ? 2.f / vtv : 0.f;
+    __syncthreads();
+    if (tid < L) {
+      const float v = tid == 0 ? v0 : x;
+      vv[tid] = v;
+      A[(k + 1 + tid) * lda + k] = v;
+    }
+    if (tid == 0) {
+      bet[k] = beta;
+      d[k] = A[k * lda + k];
+      e[k] = alpha;
+    }
+    __syncthreads();
+    if (beta != 0.f) {
+      float vp = 0;
+      for (int r0 = 0; r0 < L; r0 += nt >> 2) {   // uniform trip count: every lane joins the shuffles
+        const int r = r0 + (tid >> 2);
+        float acc = 0;
+        if (r < L) {
+          const float* Ar = A + (k + 1 + r) * lda + (k + 1);
+          float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+          int c = tid & 3;
+          for (; c + 12 < L; c += 16) {
+            acc = fmaf(Ar[c], vv[c], acc);
+            a1 = fmaf(Ar[c + 4], vv[c + 4], a1);
+            a2 = fmaf(Ar[c + 8], vv[c + 8], a2);
+            a3 = fmaf(Ar[c + 12], vv[c + 12], a3);
+          }
+          for (; c < L; c += 4) acc = fmaf(Ar[c], vv[c], acc);
+          acc += (a1 + a2) + a3;
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc *= beta;
+        if (r < L && (tid & 3) == 0) {
+          pp[r] = acc;
+          vp += vv[r] * acc;
+        }
+      }
+      const float Kc = 0.5f * beta * block_sum<float>(vp, red);
+      for (int r = tid >> 2; r < L; r += nt >> 2) {
+        const float vr = vv[r], pr = pp[r] - Kc * vr;
+        float* Ar = A + (k + 1 + r) * lda + (k + 1);
+#pragma unroll 4
+        for (int c = tid & 3; c < L; c += 4) Ar[c] -= vr * (pp[c] - Kc * vv[c]) + pr * vv[c];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    d[n - 2] = A[(n - 2) * lda + (n - 2)];
+    e[n - 2] = A[(n - 1) * lda + (n - 2)];
+    d[n - 1] = A[(n - 1) * lda + (n - 1)];
+    e[n - 1] = 0;
+  }
+  __syncthreads();
+  // ---- Q = H_0 ... H_{n-3} as Z^T (row i = column i of Q; row stride n + 1)
+  for (int idx = tid; idx < n * ldz; idx += nt) {
+    const int i = idx / ldz, j = idx - i * ldz;
+    Z[idx] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int k = n - 3; k >= 0; --k) {
+    const int L = n - k - 1;
+    if (tid < L) vv[tid] = A[(k + 1 + tid) * lda + k];
+    __syncthreads();
+    const float beta = bet[k];
+    if (beta != 0.f) {
+      for (int j0 = k + 1; j0 < n; j0 += nt >> 2) {
+        const int j = j0 + (tid >> 2);
+        float* Zj = Z + j * ldz + k + 1;
+        float t = 0;
+        if (j < n) {
+          float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+          int c = tid & 3;
+          for (; c + 12 < L; c += 16) {
+            t = fmaf(Zj[c], vv[c], t);
+            t1 = fmaf(Zj[c + 4], vv[c + 4], t1);
+            t2 = fmaf(Zj[c + 8], vv[c + 8], t2);
+            t3 = fmaf(Zj[c + 12], vv[c + 12], t3);
+          }
+          for (; c < L; c += 4) t = fmaf(Zj[c], vv[c], t);
+          t += (t1 + t2) + t3;
+        }
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t *= beta;
+        if (j < n) {
+#pragma unroll 4
+          for (int c = tid & 3; c < L; c += 4) Zj[c] -= t * vv[c];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // ---- scale T to ||T|| <= 1, split T = diag(T1, T2) + beta v v^T, v = e_{s-1} + e_s
+  const int s_split = n / 2;
+  if (tid == 0) {
+    sh_state = 0;
+    sh_done[0] = sh_done[1] = 0;
+    rcnt[0][0] = rcnt[0][1] = rcnt[1][0] = rcnt[1][1] = 0;
+    float an = 0;
+    for (int i = 0; i < n; ++i) an = fmaxf(an, fabsf(d[i]) + fabsf(e[i]) + (i ? fabsf(e[i - 1]) : 0.f));
+    sh_anorm = an;
+    const float inv = an > 0 ? 1.f / an : 1.f;
+    for (int i = 0; i < n; ++i) d[i] *= inv, e[i] *= inv;
+    const float b = e[s_split - 1];
+    sh_beta = b;
+    d[s_split - 1] -= b;
+    d[s_split] -= b;
+    e[s_split - 1] = 0.f;
+  }
+  // column n of Z carries v through the rotations of the halves: afterwards it
+  // holds z = diag(Q1, Q2)^T v
+  for (int i = tid; i < n; i += nt) Z[i * ldz + n] = (i == s_split - 1 || i == s_split) ? 1.f : 0.f;
+  __syncthreads();
+  const float scale = sh_anorm > 0 ? sh_anorm : 1.f;
+  // ---- implicit QL on both halves: warp p generates the sweeps of half p
+  {
+    int l = warp == 1 ? s_split : 0, iter = 0;
+    const int bhi = warp == 1 ? n - 1 : s_split - 1;
+    int buf = 0;
+    while (true) {
+      if (warp < 2) {
+        int cnt = 0, mm = 0;
+        while (l <= bhi) {
+          int m = bhi;
+          for (int base = l; base < bhi; base += 32) {
+            const int q = base + lane;
+            bool small = false;
+            if (q < bhi) {
+              const float em = fabsf(e[q]);
+              small = em <= eps * (fabsf(d[q]) + fabsf(d[q + 1])) || em <= eps;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, small);
+            if (bal) {
+              m = base + __ffs(bal) - 1;
+              break;
+            }
+          }
+          if (m == l) {
+            ++l;
+            iter = 0;
+            continue;
+          }
+          if (++iter > 60) {
+            if (lane == 0) sh_state = 1;
+            ++l;
+            iter = 0;
+            continue;
+          }
+          if (lane == 0) ql_sweep_chain(d, e, l, m, rc[warp][buf], rs[warp][buf], cnt);
+          cnt = __shfl_sync(0xffffffffu, cnt, 0);
+          __syncwarp();
+          mm = m;
+          break;
+        }
+        if (lane == 0) {
+          rm[warp][buf] = mm;
+          rcnt[warp][buf] = cnt;
+          sh_done[warp] = cnt == 0;
+        }
+      } else {
+        // apply the sweeps of the previous round to the columns of Z^T (and column n)
+        const int ncol = n + 1;
+        for (int idx = tid - 64; idx < 2 * ncol; idx += nt - 64) {
+          const int p = idx >= ncol ? 1 : 0, q = idx - p * ncol;
+          const int cnt = rcnt[p][buf ^ 1], m = rm[p][buf ^ 1];
+          if (cnt == 0) continue;
+          const float* cs = rc[p][buf ^ 1];
+          const float* sn = rs[p][buf ^ 1];
+          float zf = Z[m * ldz + q];
+#pragma unroll 4
+          for (int t = 0; t < cnt; ++t) {
+            const int i = m - 1 - t;
+            const float zi = Z[i * ldz + q];
+            Z[(i + 1) * ldz + q] = sn[t] * zi + cs[t] * zf;
+            zf = cs[t] * zi - sn[t] * zf;
+          }
+          Z[(m - cnt) * ldz + q] = zf;
+        }
+      }
+      __syncthreads();
+      const bool done = sh_done[0] && sh_done[1];
+      buf ^= 1;
+      __syncthreads();
+      if (done) break;
+    }
+  }
+  // ---- rank-one merge: eigenvalues of D + rho z z^T (D = d, z = Z[.][n] / sqrt 2,
+  // rho = 2 beta); for beta < 0 the problem -D + |rho| z z^T is solved and negated
+  const float beta0 = sh_beta;
+  if (beta0 != 0.f) {
+    const bool neg = beta0 < 0.f;
+    const float rho = 2.f * fabsf(beta0);
+    const float rs2 = 0.70710678118654752f;
+    for (int i = tid; i < n; i += nt) {
+      const float di = neg ? -d[i] : d[i];
+      int rank = 0;
+      for (int j = 0; j < n; ++j) {
+        const float dj = neg ? -d[j] : d[j];
+        rank += (dj < di) || (dj == di && j < i);
+      }
+      perm[rank] = i;
+      ds[rank] = di;
+      zs[rank] = Z[i * ldz + n] * rs2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // deflation (LAPACK DLAED2's rules): a negligible component leaves d_r as an
+      // eigenvalue; two close poles are rotated so that one component vanishes
+      float dmax = 0, zmax = 0;
+      for (int r = 0; r < n; ++r) dmax = fmaxf(dmax, fabsf(ds[r])), zmax = fmaxf(zmax, fabsf(zs[r]));
+      const float tol = 8.f * eps * fmaxf(dmax, rho * zmax);
+      int K = 0, nrot = 0, prev = -1;
+      for (int r = 0; r < n; ++r) {
+        if (rho * fabsf(zs[r]) <= tol) continue;
+        if (prev >= 0) {
+          const float zp = zs[prev], zr = zs[r];
+          const float t = hypotf(zp, zr);
+          const float c = zr / t, sg = -zp / t;
+          const float off = (ds[r] - ds[prev]) * c * sg;
+          if (fabsf(off) <= tol) {
+            // rotate (prev, r): z_prev -> 0, z_r -> t; prev leaves as deflated
+            zs[r] = t;
+            zs[prev] = 0.f;
+            const float dp = ds[prev], dr = ds[r];
+            ds[prev] = dp * c * c + dr * sg * sg;
+            ds[r] = dp * sg * sg + dr * c * c;
+            rot_a[nrot] = perm[prev];
+            rot_b[nrot] = perm[r];
+            rot_c[nrot] = c;
+            rot_s[nrot] = sg;
+            ++nrot;
+            --K;   // prev was counted
+            prev = r;
+            kidx[K++] = r;
+            continue;
+          }
+        }
+        prev = r;
+        kidx[K++] = r;
+      }
+      sh_K = K;
+      sh_nrot = nrot;
+    }
+    __syncthreads();
+    const int K = sh_K, nrot = sh_nrot;
+    // the deflating rotations act on the vectors (rows of Z^T), in order
+    if (warp == 0) {
+      for (int t = 0; t < nrot; ++t) {
+        const int a = rot_a[t], b = rot_b[t];
+        const float c = rot_c[t], sg = rot_s[t];
+        for (int q = lane; q < n; q += 32) {
+          const float xa = Z[a * ldz + q], xb = Z[b * ldz + q];
+          Z[a * ldz + q] = c * xa + sg * xb;
+          Z[b * ldz + q] = c * xb - sg * xa;
+        }
+        __syncwarp();
+      }
+    }
+    for (int j = tid; j < K; j += nt) {
+      dk[j] = ds[kidx[j]];
+      zk[j] = zs[kidx[j]];
+    }
+    __syncthreads();
+    // secular equation f(x) = 1 + rho sum_i zk_i^2 / (dk_i - x) = 0, one root per
+    // interval (dk_j, dk_j+1), the last in (dk_K-1, dk_K-1 + rho |zk|^2); each
+    // root is found as an offset tau from the nearer pole dk_org by Newton's
+    // method on f inside a bracket that every step narrows (bisection where a
+    // Newton step would leave it); two threads per root split the sums
+    float zz = 0.f;
+    for (int i = 0; i < K; ++i) zz += zk[i] * zk[i];
+    for (int j0 = 0; j0 < K; j0 += nt >> 1) {   // uniform trip count: both threads of a pair join the shuffles
+      const int j = j0 + (tid >> 1), h = tid & 1;
+      const bool act = j < K;
+      const bool inner = act && j < K - 1;
+      const float w = inner ? dk[j + 1] - dk[j] : 0.f;
+      float fmid = 0.f;
+      if (inner)
+        for (int i = h; i < K; i += 2) fmid += zk[i] * zk[i] / ((dk[i] - dk[j]) - 0.5f * w);
+      fmid += __shfl_xor_sync(0xffffffffu, fmid, 1);
+      int o = 0;
+      float lo = 0.f, hi = 0.f;
+      if (inner) {
+        if (1.f + rho * fmid >= 0.f) {
+          o = j;
+          hi = 0.5f * w;
+        } else {
+          o = j + 1;
+          lo = -0.5f * w;
+        }
+      } else if (act) {
+        o = K - 1;
+        hi = rho * zz * 1.0001f;
+      }
+      const float dorg = act ? dk[o] : 0.f;
+      float t = 0.5f * (lo + hi);
+      for (int it = 0; it < 40; ++it) {
+        float f = 0.f, fp = 0.f;
+        if (act)
+          for (int i = h; i < K; i += 2) {
+            const float rcp = __fdividef(1.f, (dk[i] - dorg) - t);
+            const float zr = zk[i] * rcp;
+            f = fmaf(zk[i], zr, f);
+            fp = fmaf(zr, zr, fp);
+          }
+        f += __shfl_xor_sync(0xffffffffu, f, 1);
+        fp += __shfl_xor_sync(0xffffffffu, fp, 1);
+        bool stop = true;
+        if (act) {
+          const float F = fmaf(rho, f, 1.f);
+          if (F < 0.f) lo = t;
+          else hi = t;
+          float tn = t - F / (rho * fp);
+          if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+          stop = fabsf(tn - t) <= 2.f * eps * fmaxf(fabsf(t), fabsf(tn)) || hi - lo <= 2.f * eps * fmaxf(fabsf(lo), fabsf(hi));
+          t = tn;
+        }
+        if (__all_sync(0xffffffffu, stop)) break;
+      }
+      if (act && h == 0) {
+        org[j] = o;
+        tau[j] = t;
+        lam[j] = dorg + t;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < K; i += nt) {
+      float prod = ((dk[org[K - 1]] - dk[i]) + tau[K - 1]) / rho;
+      for (int k = 0; k < i; ++k) prod *= __fdividef((dk[org[k]] - dk[i]) + tau[k], dk[k] - dk[i]);
+      for (int k = i; k < K - 1; ++k) prod *= __fdividef((dk[org[k]] - dk[i]) + tau[k], dk[k + 1] - dk[i]);
+      zhat[i] = copysignf(sqrtf(fmaxf(prod, 0.f)), zk[i]);
+    }
+    __syncthreads();
+    // merged vectors: u_j(i) = zhat_i / (dk_i - lam_j), normalised, as row j of
+    // W (shared memory, in A's place)
+    float* W = A;
+    for (int j = tid; j < K; j += nt) {
+      const float dorg = dk[org[j]], tj = tau[j];
+      float nrm = 0.f;
+      for (int i = 0; i < K; ++i) {
+        const float u = __fdividef(zhat[i], (dk[i] - dorg) - tj);
+        W[j * K + i] = u;
+        nrm = fmaf(u, u, nrm);
+      }
+      const float inv = rsqrtf(nrm);
+      for (int i = 0; i < K; ++i) W[j * K + i] *= inv;
+    }
+    for (int i = tid; i < K; i += nt) kslot[i] = perm[kidx[i]];
+    __syncthreads();
+    // new rows j = sum_i u_j(i) row(slot_i), four rows j per thread, through
+    // global scratch (Z is read until every product is formed)
+    const int nb = (K + 3) / 4;
+    for (int o = tid; o < nb * n; o += nt) {
+      const int jb = o / n, q = o - jb * n, j0 = 4 * jb;
+      const int j1 = min(j0 + 1, K - 1), j2 = min(j0 + 2, K - 1), j3 = min(j0 + 3, K - 1);
+      float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 4
+      for (int i = 0; i < K; ++i) {
+        const float z = Z[kslot[i] * ldz + q];
+        a0 = fmaf(W[j0 * K + i], z, a0);
+        a1 = fmaf(W[j1 * K + i], z, a1);
+        a2 = fmaf(W[j2 * K + i], z, a2);
+        a3 = fmaf(W[j3 * K + i], z, a3);
+      }
+      gW[(size_t)j0 * n + q] = a0;
+      if (j0 + 1 < K) gW[(size_t)(j0 + 1) * n + q] = a1;
+      if (j0 + 2 < K) gW[(size_t)(j0 + 2) * n + q] = a2;
+      if (j0 + 3 < K) gW[(size_t)(j0 + 3) * n + q] = a3;
+    }
+    __syncthreads();
+    for (int o = tid; o < K * n; o += nt) {
+      const int j = o / n, q = o - j * n;
+      Z[kslot[j] * ldz + q] = gW[o];
+    }
+    // eigenvalues back in the original order of the rows
+    for (int r = tid; r < n; r += nt) d[perm[r]] = neg ? -ds[r] : ds[r];
+    __syncthreads();
+    for (int j = tid; j < K; j += nt) d[perm[kidx[j]]] = neg ? -lam[j] : lam[j];
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) d[i] *= scale;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    const float di = d[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const float dj = d[j];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    evals[rank] = (double)di;
+    if (!isfinite((double)di)) atomicOr(status, 2);
+    for (int q = 0; q < n; ++q) evecs[q * n + rank] = (double)Z[i * ldz + q];
+  }
+  if (tid == 0 && sh_state) atomicOr(status, 1);
+}
+
+
 // ---------------------------------------------------------------- parallel Jacobi (FP32)
 // Two-sided cyclic Jacobi with the round-robin ordering: in each round the
 // n/2 disjoint pairs (p, q) are rotated at once (rotation angles from the
@@ -994,6 +1488,23 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
     return;
   }
   const bool dbl = mode != kEigFast;
+  if (!dbl && n >= kDcMin && n <= kDcMax) {
+    // one divide-and-conquer level (k_sym_eig_dc); its merge writes through
+    // global scratch of n x n floats
+    w.status.alloc(1);
+    BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
+    DevBuf<double>& gbuf = h.sc.eig_glob;
+    gbuf.alloc(2 * (size_t)kEigMax * kEigMax);
+    allow_max_smem((const void*)k_sym_eig_dc);
+    const size_t smem = (size_t)2 * n * dc_ld(n) * sizeof(float);
+    BM_LAUNCH(h, "sym_eig_f32", k_sym_eig_dc<<<1, kEigThreads, smem, h.stream>>>(
+                                    S, n, evals, evecs, reinterpret_cast<float*>(gbuf.get()), w.status.get()));
+    int st = 0;
+    BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    BM_CUDA(cudaStreamSynchronize(h.stream));
+    BM_REQUIRE(st == 0, BM_ERR_NUMERIC, st & 2 ? "eigensolver: non-finite eigenvalue" : "eigensolver: QL did not converge");
+    return;
+  }
   const size_t es = dbl ? 8 : 4;
   const size_t nn = (size_t)n * n * es;
   const size_t cap = 200 * 1024;

@@ -49,8 +49,11 @@ constexpr int kSpmmCols = 256;
 void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall& Out, float gamma);
 
 // Accuracy modes of the symmetric eigensolver.
-//  kEigFast: FP32 Householder + QL; eigenvalue errors ~ eps32 * ||S||.
-//  kEigRelative: kEigFast vectors V, S' = V^T S V in FP64, then FP32 Jacobi
+//  kEigFast: FP32 Householder tridiagonalisation, then implicit QL, with one
+//    divide-and-conquer level for 24 <= n <= 150 (the halves by QL, merged
+//    through the secular equation); eigenvalue errors ~ eps32 * ||S||.
+//  kEigRelative: kEigFast vectors V0, one FP64 Newton-Schulz step to an
+//    orthogonal V, S' = V^T S V in FP64, then FP32 Jacobi
 //    sweeps on S' with the relative rotation test |s_pq| > eps sqrt(s_pp s_qq);
 //    for positive semidefinite S this resolves each eigenvalue to a relative
 //    accuracy set by the conditioning of the diagonally scaled S' (Demmel and
