@@ -1168,45 +1168,65 @@ __global__ void k_small_mm_tn(const double* __restrict__ A, const double* __rest
 
 // ---------------------------------------------------------------- Cholesky QR step
 // T = R^{-1} with R^T R = S (upper Cholesky factor), S symmetric positive
-// definite (the Gram of an almost orthonormal block).  One block, FP32,
-// right-looking factorisation then one column of the inverse per thread.
+// definite (the Gram of an almost orthonormal block).  One block, FP32.  The
+// right-looking factorisation updates the upper triangle of the Schur
+// complement, A_rc -= A_jr A_jc / A_jj (four threads to a row, one barrier
+// per column), and scales the rows by 1 / sqrt(A_jj) at the end; the inverse
+// is formed column by column (one thread per column, back substitution) in
+// shared memory when it fits, else in T.
+__host__ __device__ constexpr int chol_ld(int n) { return ((n + 27) / 32) * 32 + 4; }
+
 __global__ void __launch_bounds__(512) k_chol_inv(const double* __restrict__ S, int n, float* __restrict__ T, int ldt,
-                                                int* __restrict__ status, double* __restrict__ inv_fro2) {
+                                                int* __restrict__ status, double* __restrict__ inv_fro2, int x_smem) {
   extern __shared__ __align__(16) float ch_sm[];
-  float* A = ch_sm;  // n x n, upper triangle holds R
+  const int lda = chol_ld(n);
+  float* A = ch_sm;                       // n x lda, upper triangle becomes R
+  float* X = x_smem ? A + (size_t)n * lda : T;
+  const int ldx = x_smem ? lda : ldt;
   const int tid = threadIdx.x, nt = blockDim.x;
-  __shared__ float piv;
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx - i * n;
-    A[idx] = (float)(0.5 * (S[i * n + j] + S[j * n + i]));
+    A[i * lda + j] = (float)(0.5 * (S[i * n + j] + S[j * n + i]));
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const float a = A[j * n + j];
-      if (!(a > 0.f)) atomicOr(status, 8);
-      piv = a > 0.f ? sqrtf(a) : 1.f;
-      A[j * n + j] = piv;
-    }
-    __syncthreads();
-    for (int c = j + 1 + tid; c < n; c += nt) A[j * n + c] /= piv;
-    __syncthreads();
-    const int L = n - j - 1;
-    for (int idx = tid; idx < L * L; idx += nt) {
-      const int r = j + 1 + idx / L, c = j + 1 + idx % L;
-      if (c >= r) A[r * n + c] -= A[j * n + r] * A[j * n + c];
+    const float a = A[j * lda + j];
+    if (tid == 0 && !(a > 0.f)) atomicOr(status, 8);
+    const float inv = a > 0.f ? 1.f / a : 0.f;
+    const float* Aj = A + j * lda;
+    for (int r = j + 1 + (tid >> 2); r < n; r += nt >> 2) {
+      const float f = Aj[r] * inv;
+      float* Ar = A + r * lda;
+#pragma unroll 4
+      for (int c = r + (tid & 3); c < n; c += 4) Ar[c] = fmaf(-f, Aj[c], Ar[c]);
     }
     __syncthreads();
   }
-  // X = R^{-1}: column c solves R x = e_c by back substitution (thread per
-  // column); ||R^{-1}||_F^2 is summed on the way
+  for (int j = tid; j < n; j += nt) {
+    const float a = A[j * lda + j];
+    const float rs = a > 0.f ? rsqrtf(a) : 1.f;
+    for (int c = j + 1; c < n; ++c) A[j * lda + c] *= rs;
+    A[j * lda + j] = a > 0.f ? a * rs : 1.f;
+  }
+  __syncthreads();
+  // X = R^{-1}: column c solves R x = e_c by back substitution; ||R^{-1}||_F^2
+  // is summed on the way
   double sq = 0.0;
   for (int c = tid; c < n; c += nt) {
-    for (int i = n - 1; i >= 0; --i) {
-      float acc = (i == c) ? 1.f : 0.f;
-      for (int k = i + 1; k <= c; ++k) acc -= A[i * n + k] * T[k * ldt + c];
-      const float x = i > c ? 0.f : acc / A[i * n + i];
-      T[i * ldt + c] = x;
+    for (int i = n - 1; i > c; --i) X[i * ldx + c] = 0.f;
+    for (int i = c; i >= 0; --i) {
+      const float* Ri = A + i * lda;
+      float a0 = (i == c) ? 1.f : 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      int k = i + 1;
+      for (; k + 3 <= c; k += 4) {
+        a0 = fmaf(-Ri[k], X[k * ldx + c], a0);
+        a1 = fmaf(-Ri[k + 1], X[(k + 1) * ldx + c], a1);
+        a2 = fmaf(-Ri[k + 2], X[(k + 2) * ldx + c], a2);
+        a3 = fmaf(-Ri[k + 3], X[(k + 3) * ldx + c], a3);
+      }
+      for (; k <= c; ++k) a0 = fmaf(-Ri[k], X[k * ldx + c], a0);
+      const float x = ((a0 + a1) + (a2 + a3)) / Ri[i];
+      X[i * ldx + c] = x;
       sq += (double)x * (double)x;
     }
   }
@@ -1226,10 +1246,10 @@ __global__ void __launch_bounds__(512) k_chol_inv(const double* __restrict__ S, 
   for (int idx = tid; idx < n * ldt; idx += nt) {
     const int i = idx / ldt, c = idx - i * ldt;
     if (c >= n) T[idx] = 0.f;
+    else if (x_smem) T[idx] = X[i * ldx + c];
   }
 }
 
-// ---------------------------------------------------------------- small helpers
 __global__ void k_select_scale(const double* __restrict__ E, int n, int rows, const int* __restrict__ cols,
                                const double* __restrict__ scale, int ncols, float* __restrict__ T, int ldt) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * ldt; idx += gridDim.x * blockDim.x) {
@@ -1539,13 +1559,15 @@ namespace {
 // Returns the status word (0: R^{-1} in T) and, with fro2, ||R^{-1}||_F^2.
 int chol_inv_run(bm_ctx& h, DenseWork& w, const double* S, int n, float* T, int ldt, double* fro2) {
   BM_REQUIRE(n >= 1 && n <= 200, BM_ERR_INVALID, "cholesky: size out of range");
-  const size_t smem = (size_t)n * n * sizeof(float);
+  const size_t one = (size_t)n * chol_ld(n) * sizeof(float);
+  const int x_smem = 2 * one <= 200 * 1024 ? 1 : 0;   // R^{-1} in shared memory beside R when it fits
+  const size_t smem = (1 + x_smem) * one;
   w.status.alloc(1);
   w.scratch.alloc(1);
   BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
   allow_max_smem((const void*)k_chol_inv);
   BM_LAUNCH(h, "chol_inv", k_chol_inv<<<1, 512, smem, h.stream>>>(S, n, T, ldt, w.status.get(),
-                                                                  fro2 ? w.scratch.get() : nullptr));
+                                                                  fro2 ? w.scratch.get() : nullptr, x_smem));
   int st = 0;
   BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
   if (fro2) BM_CUDA(cudaMemcpyAsync(fro2, w.scratch.get(), sizeof(double), cudaMemcpyDeviceToHost, h.stream));
