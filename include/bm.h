@@ -376,6 +376,24 @@ bm_status bm_batch_create(bm_handle* hs, int32_t count, bm_batch* out);
 void bm_batch_destroy(bm_batch b);
 const char* bm_batch_last_error(bm_batch b);
 bm_status bm_batch_bm_phase(bm_batch b, int32_t epochs, double* F);
+/*
+ * bm_batch_prox_step -- one inexact PG step (Eq. "inexactpg", as
+ * bm_prox_step with step size alpha, <= 0: each handle's option) on every
+ * handle of the batch at once.  Each handle's step runs on its own host
+ * thread and stream; the q-wide residual SpMMs of Eq. "ZZ" (the sparse part
+ * of the products Z^T U and Z Y of Algorithm 2) meet: when every handle
+ * still inside its step has one ready, they run as shared launches over the
+ * concatenated segment lists (one per orientation, row width and layout),
+ * and the results are bit for bit those of bm_prox_step.  Handles of any rank
+ * may take part.  info (bm_prox_info[count], nullable) receives each
+ * handle's result.  Errors: the first failing handle's status, with its
+ * message in bm_batch_last_error.
+ *
+ * bm_batch_stats -- the products handed to the shared launches so far and
+ * the launches made for them (nullable outputs).
+ */
+bm_status bm_batch_prox_step(bm_batch b, double alpha, bm_prox_info* info);
+bm_status bm_batch_stats(bm_batch b, int64_t* spmm_products, int64_t* spmm_launches);
 
 /*
  * Serving: a continuous-batching request loop for many completion solves.

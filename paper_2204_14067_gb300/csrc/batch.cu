@@ -11,10 +11,13 @@
 #include <algorithm>
 #include <cmath>
 #include <memory>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_bf16.h>
 
+#include "dense.cuh"
 #include "pipe.cuh"
 #include "quartic.cuh"
 
@@ -282,6 +285,7 @@ struct bm_batch_ctx {
   DevBuf<double> part, scal;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  bm::SpmmCombiner* comb = nullptr;  // shared SpMM launches of bm_batch_prox_step
   std::string err;
 };
 
@@ -544,6 +548,7 @@ void bm_batch_destroy(bm_batch b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graph(*b);
+  spmm_combiner_destroy(b->comb);
   cudaStream_t s = b->stream;
   delete b;
   if (s) cudaStreamDestroy(s);
@@ -602,6 +607,44 @@ bm_status bm_batch_bm_phase(bm_batch b, int32_t epochs, double* F) {
       if (F) F[p] = Fp;
     }
   });
+}
+
+bm_status bm_batch_prox_step(bm_batch b, double alpha, bm_prox_info* info) {
+  if (!b) return BM_ERR_INVALID;
+  return batch_guarded(b, [&] {
+    for (int p = 0; p < b->count; ++p)
+      BM_REQUIRE(!b->hs[p]->comb, BM_ERR_INVALID, "bm_batch_prox_step: a handle is already in a batched PG step");
+    if (!b->comb) b->comb = spmm_combiner_create(b->count);
+    spmm_combiner_begin(b->comb, b->count);
+    for (int p = 0; p < b->count; ++p) b->hs[p]->comb = b->comb;
+    int dev = 0;
+    BM_CUDA(cudaGetDevice(&dev));
+    std::vector<bm_status> st(b->count, BM_OK);
+    std::vector<bm_prox_info> tmp(b->count);
+    {
+      // one host thread per handle: each runs its PG step on its own stream,
+      // the residual SpMMs meet in the combiner
+      std::vector<std::thread> th;
+      for (int p = 0; p < b->count; ++p)
+        th.emplace_back([&, p] {
+          cudaSetDevice(dev);
+          st[p] = bm_prox_step(b->hs[p], alpha, info ? &info[p] : &tmp[p]);
+          spmm_combiner_leave(b->comb);
+        });
+      for (auto& t : th) t.join();
+    }
+    for (int p = 0; p < b->count; ++p) b->hs[p]->comb = nullptr;
+    for (int p = 0; p < b->count; ++p)
+      if (st[p] != BM_OK)
+        throw Error{st[p], "bm_batch_prox_step: handle " + std::to_string(p) + ": " + b->hs[p]->err};
+  });
+}
+
+bm_status bm_batch_stats(bm_batch b, int64_t* spmm_products, int64_t* spmm_launches) {
+  if (!b) return BM_ERR_INVALID;
+  if (spmm_products) *spmm_products = spmm_combiner_products(b->comb);
+  if (spmm_launches) *spmm_launches = spmm_combiner_launches(b->comb);
+  return BM_OK;
 }
 
 }  // extern "C"

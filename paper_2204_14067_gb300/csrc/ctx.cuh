@@ -100,6 +100,7 @@ struct Scratch {
 struct ProxState;  // defined in prox.cu
 struct BbState;    // defined in sparsa.cu (SpaRSA step rule)
 struct BcdState;   // defined in bcd.cu (column-block BM solver)
+struct SpmmCombiner;  // defined in dense.cu (shared SpMM launches of batched PG steps)
 
 // Optional per-kernel event timing (bm_profile_enable).
 struct Profiler {
@@ -136,6 +137,7 @@ struct bm_ctx {
   bm::ProxState* ps = nullptr;
   bm::BbState* bb = nullptr;     // SpaRSA step-rule state (created on first use)
   bm::BcdState* bcd = nullptr;   // column-block BM solver scratch (created on first use)
+  bm::SpmmCombiner* comb = nullptr;  // set while a batched PG step runs: SpMMs go through it
   bm::Profiler prof;
   std::string err;
   bool bm_changed = false;       // BM phase moved since the last PG step

@@ -3,6 +3,12 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <condition_variable>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "dense.cuh"
 #include "pipe.cuh"
@@ -1426,7 +1432,190 @@ void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, 
                                                                    beta, gamma, groups));
 }
 
+// ---------------------------------------------------------------- shared SpMM launches
+struct SpmmCombiner {
+  struct Req {
+    bm_ctx* h;
+    bool csr;
+    const float* vals;
+    Tall X, Out;
+    float gamma;
+  };
+  std::mutex mu;
+  std::condition_variable cv;
+  int live = 0;
+  uint64_t gen = 0;
+  std::vector<Req> pending;
+  std::map<bm_ctx*, cudaEvent_t> ready;   // per participant: its stream's work so far
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+  DevBuf<PipeArgs> args_d;
+  DevBuf<int64_t> prefix_d;
+  int cap = 0;                             // slices the device tables hold
+  bm_status fail = BM_OK;
+  std::string fail_msg;
+  int64_t launches = 0;   // batched SpMM launches
+  int64_t products = 0;   // products handed in
+
+  // Launch every pending product (called with mu held by the last arrival).
+  void launch_all() {
+    fail = BM_OK;
+    try {
+      for (const Req& r : pending) BM_CUDA(cudaStreamWaitEvent(st, ready.at(r.h), 0));
+      struct Slice {
+        const Req* r;
+        PipeArgs a;
+        bool ws;
+        int cols;
+        const Segs* sg;
+      };
+      std::vector<Slice> sl;
+      for (const Req& r : pending) {
+        const Index& ix = r.h->ix;
+        const int kind = r.csr ? kPassSpmmCsr : kPassSpmmCsc;
+        const Segs& sg = pass_segs(ix, kind);
+        for (int c0 = 0; c0 < r.X.cols; c0 += kSpmmCols) {
+          const int cols = std::min(kSpmmCols, r.X.cols - c0);
+          PipeArgs a{};
+          a.seg_row = sg.row.get();
+          a.seg_beg = sg.beg.get();
+          a.seg_end = sg.end.get();
+          a.seg_slot = sg.slot.get();
+          a.nseg = sg.nseg;
+          a.idx = r.csr ? ix.col.get() : ix.row.get();
+          a.scal = r.vals;
+          a.g0 = r.X.p + c0;
+          a.ld = r.X.ld;
+          a.nchunk = (cols + 3) / 4;
+          a.gamma = r.gamma;
+          a.out = r.Out.p + c0;
+          a.ld_out = r.Out.ld;
+          a.partial = r.h->sc.partial.get();
+          a.ld_part = 4 * a.nchunk;
+          BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ld_part <= (int64_t)r.h->sc.partial.n,
+                     BM_ERR_INVALID, "spmm: partial buffer too small");
+          sl.push_back({&r, a, pass_ws(ix, kind), cols, &sg});
+        }
+      }
+      // one launch per (orientation, row width, layout)
+      std::stable_sort(sl.begin(), sl.end(), [](const Slice& x, const Slice& y) {
+        return std::make_tuple(x.r->csr, x.a.nchunk, x.ws) < std::make_tuple(y.r->csr, y.a.nchunk, y.ws);
+      });
+      if ((int)sl.size() > cap) throw Error{BM_ERR_INVALID, "spmm combiner: more products than the tables hold"};
+      std::vector<PipeArgs> A;
+      std::vector<int64_t> P;
+      size_t off = 0, poff = 0;
+      for (size_t g0 = 0; g0 < sl.size();) {
+        size_t g1 = g0 + 1;
+        while (g1 < sl.size() && sl[g1].r->csr == sl[g0].r->csr && sl[g1].a.nchunk == sl[g0].a.nchunk &&
+               sl[g1].ws == sl[g0].ws)
+          ++g1;
+        A.clear();
+        P.assign(1, 0);
+        for (size_t i = g0; i < g1; ++i) {
+          A.push_back(sl[i].a);
+          P.push_back(P.back() + sl[i].a.nseg);
+        }
+        // pageable sources: the copies are staged before the calls return
+        BM_CUDA(cudaMemcpyAsync(args_d.get() + off, A.data(), A.size() * sizeof(PipeArgs), cudaMemcpyHostToDevice,
+                                st));
+        BM_CUDA(cudaMemcpyAsync(prefix_d.get() + poff, P.data(), P.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                st));
+        launch_direct_batch<1>(args_d.get() + off, prefix_d.get() + poff, (int)A.size(), P.back(),
+                               sl[g0].a.nchunk, false, sl[g0].ws, st);
+        BM_CHECK_LAUNCH();
+        ++launches;
+        off += A.size();
+        poff += P.size();
+        g0 = g1;
+      }
+      for (const Slice& x : sl) {
+        const Segs& sg = *x.sg;
+        if (!sg.nmulti) continue;
+        k_spmm_fixup<<<grid1(sg.nmulti * x.cols), 256, 0, st>>>(sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(),
+                                                                 sg.nmulti, x.a.partial, x.a.ld_part, x.cols,
+                                                                 x.a.gamma, x.a.out, x.a.ld_out);
+        BM_CHECK_LAUNCH();
+      }
+      BM_CUDA(cudaEventRecord(done, st));
+    } catch (const Error& e) {
+      fail = e.code;
+      fail_msg = e.msg;
+    } catch (...) {
+      fail = BM_ERR_CUDA;
+      fail_msg = "spmm combiner: launch failed";
+    }
+    pending.clear();
+    ++gen;
+    cv.notify_all();
+  }
+};
+
+SpmmCombiner* spmm_combiner_create(int participants_max) {
+  auto c = std::make_unique<SpmmCombiner>();
+  BM_CUDA(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+  BM_CUDA(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+  // at most two column slices per product (q <= 2 kSpmmCols)
+  c->cap = 2 * std::max(1, participants_max);
+  c->args_d.alloc((size_t)c->cap);
+  c->prefix_d.alloc((size_t)2 * c->cap);
+  return c.release();
+}
+
+void spmm_combiner_destroy(SpmmCombiner* c) {
+  if (!c) return;
+  if (c->st) {
+    cudaStreamSynchronize(c->st);
+    cudaStreamDestroy(c->st);
+  }
+  if (c->done) cudaEventDestroy(c->done);
+  for (auto& kv : c->ready) cudaEventDestroy(kv.second);
+  delete c;
+}
+
+void spmm_combiner_begin(SpmmCombiner* c, int participants) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->live = participants;
+  c->pending.clear();
+}
+
+void spmm_combiner_leave(SpmmCombiner* c) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  --c->live;
+  if (c->live > 0 && (int)c->pending.size() == c->live) c->launch_all();
+}
+
+int64_t spmm_combiner_launches(const SpmmCombiner* c) { return c ? c->launches : 0; }
+int64_t spmm_combiner_products(const SpmmCombiner* c) { return c ? c->products : 0; }
+
+namespace {
+void spmm_combined(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall& Out, float gamma) {
+  SpmmCombiner& c = *h.comb;
+  std::unique_lock<std::mutex> lk(c.mu);
+  auto it = c.ready.find(&h);
+  if (it == c.ready.end()) {
+    cudaEvent_t ev = nullptr;
+    BM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    it = c.ready.emplace(&h, ev).first;
+  }
+  BM_CUDA(cudaEventRecord(it->second, h.stream));
+  c.pending.push_back({&h, csr, vals, X, Out, gamma});
+  ++c.products;
+  const uint64_t g = c.gen;
+  if ((int)c.pending.size() == c.live) c.launch_all();
+  else c.cv.wait(lk, [&] { return c.gen != g; });
+  if (c.fail != BM_OK) throw Error{c.fail, c.fail_msg};
+  // before the next generation can re-record it (that needs this thread back)
+  BM_CUDA(cudaStreamWaitEvent(h.stream, c.done, 0));
+}
+}  // namespace
+
 void spmm_dev(bm_ctx& h, bool csr, const float* vals, const Tall& X, const Tall& Out, float gamma) {
+  if (X.cols == 0) return;
+  if (h.comb) {
+    spmm_combined(h, csr, vals, X, Out, gamma);
+    return;
+  }
   const Index& ix = h.ix;
   const Segs& sg = pass_segs(ix, csr ? kPassSpmmCsr : kPassSpmmCsc);
   if (X.cols == 0) return;

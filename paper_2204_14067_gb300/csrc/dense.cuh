@@ -42,6 +42,23 @@ void gram_reduce_dev(bm_ctx& h, const float2* part, int slabs, int a, int b, int
 void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, float beta, float gamma,
               const char* tag);
 
+// Shared launches of the q-wide residual SpMMs of several handles' PG steps,
+// each running on its own host thread and stream (bm_batch_prox_step).  While
+// h.comb is set, spmm_dev hands its product to the combiner and waits: when
+// every participant still inside its PG step has handed one in, the last to
+// arrive launches them all as batched passes over the concatenated segment
+// lists (one launch per orientation, row width and layout) on the
+// combiner's stream, ordered after each participant's earlier work, and each
+// participant's stream then waits for them.  A participant that finishes its
+// PG step calls spmm_combiner_leave.  The products are the same, bit for
+// bit, as those of separate launches.
+SpmmCombiner* spmm_combiner_create(int participants_max);
+void spmm_combiner_destroy(SpmmCombiner* c);
+void spmm_combiner_begin(SpmmCombiner* c, int participants);
+void spmm_combiner_leave(SpmmCombiner* c);
+int64_t spmm_combiner_launches(const SpmmCombiner* c);   // batched launches so far
+int64_t spmm_combiner_products(const SpmmCombiner* c);   // products handed in so far
+
 // Sparse part of Z products: Out(i,:) += gamma * sum_e v_e X(idx_e,:) over a
 // segment split (CSR: i = row, idx = col; CSC: i = col, idx = row).  Blocks
 // wider than kSpmmCols run as several launches over column slices.
