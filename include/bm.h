@@ -386,13 +386,14 @@ bm_status bm_batch_bm_phase(bm_batch b, int32_t epochs, double* F);
  * concatenated segment lists (one per orientation, row width and layout),
  * and the results are bit for bit those of bm_prox_step.  Handles of any rank
  * may take part.  info (bm_prox_info[count], nullable) receives each
- * handle's result.  Errors: the first failing handle's status, with its
- * message in bm_batch_last_error.
+ * handle's result, status (bm_status[count], nullable) each handle's status
+ * (a failing handle does not stop the others).  Errors: the first failing
+ * handle's status, with its message in bm_batch_last_error.
  *
  * bm_batch_stats -- the products handed to the shared launches so far and
  * the launches made for them (nullable outputs).
  */
-bm_status bm_batch_prox_step(bm_batch b, double alpha, bm_prox_info* info);
+bm_status bm_batch_prox_step(bm_batch b, double alpha, bm_prox_info* info, bm_status* status);
 bm_status bm_batch_stats(bm_batch b, int64_t* spmm_products, int64_t* spmm_launches);
 
 /*
@@ -405,7 +406,10 @@ bm_status bm_batch_stats(bm_batch b, int64_t* spmm_products, int64_t* spmm_launc
  * (bm_create + bm_init with the server's precision) and stays resident
  * until it finishes.  batched = 1: every cycle runs the BM phases (3
  * iterations) of all active solves as one bm_batch and then their PG steps
- * concurrently from `workers` host threads; a solve finishes when the
+ * concurrently from `workers` host threads, each on its own stream (measured
+ * faster here than bm_batch_prox_step's shared SpMM launches, whose
+ * rendezvous holds every solve to the slowest one's pace); a solve finishes
+ * when the
  * relative change of F between cycles is below tol or after max_outer
  * cycles, and requests that arrived meanwhile join at the next cycle.
  * batched = 0: one solve at a time with bm_solve.

@@ -563,7 +563,7 @@ _SIGS.update({
     "bm_batch_destroy": (None, [_P]),
     "bm_batch_last_error": (_c.c_char_p, [_P]),
     "bm_batch_bm_phase": (_c.c_int, [_P, _c.c_int32, _P]),
-    "bm_batch_prox_step": (_c.c_int, [_P, _c.c_double, _c.POINTER(bm_prox_info)]),
+    "bm_batch_prox_step": (_c.c_int, [_P, _c.c_double, _c.POINTER(bm_prox_info), _P]),
     "bm_batch_stats": (_c.c_int, [_P, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
 })
 
@@ -594,7 +594,7 @@ def bm_batch_bm_phase(b, count, epochs):
 def bm_batch_prox_step(b, count, alpha=0.0):
     """One PG step on every handle of the batch (shared SpMM launches); a list of info dicts."""
     infos = (bm_prox_info * count)()
-    _check_batch(lib().bm_batch_prox_step(b, float(alpha), infos), b)
+    _check_batch(lib().bm_batch_prox_step(b, float(alpha), infos, None), b)
     return [_info_dict(infos[i]) for i in range(count)]
 
 

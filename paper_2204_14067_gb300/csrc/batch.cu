@@ -609,7 +609,7 @@ bm_status bm_batch_bm_phase(bm_batch b, int32_t epochs, double* F) {
   });
 }
 
-bm_status bm_batch_prox_step(bm_batch b, double alpha, bm_prox_info* info) {
+bm_status bm_batch_prox_step(bm_batch b, double alpha, bm_prox_info* info, bm_status* status) {
   if (!b) return BM_ERR_INVALID;
   return batch_guarded(b, [&] {
     for (int p = 0; p < b->count; ++p)
@@ -634,6 +634,8 @@ bm_status bm_batch_prox_step(bm_batch b, double alpha, bm_prox_info* info) {
       for (auto& t : th) t.join();
     }
     for (int p = 0; p < b->count; ++p) b->hs[p]->comb = nullptr;
+    if (status)
+      for (int p = 0; p < b->count; ++p) status[p] = st[p];
     for (int p = 0; p < b->count; ++p)
       if (st[p] != BM_OK)
         throw Error{st[p], "bm_batch_prox_step: handle " + std::to_string(p) + ": " + b->hs[p]->err};

@@ -2,6 +2,7 @@
 // one-CTA symmetric eigensolver and small helpers of the proximal step.
 #include <algorithm>
 #include <cfloat>
+#include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <map>
@@ -1433,6 +1434,10 @@ void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, 
 }
 
 // ---------------------------------------------------------------- shared SpMM launches
+// Longest time a product waits for the other participants' products before
+// the products that have arrived are launched without them.
+constexpr int kCombineWaitUs = 100;
+
 struct SpmmCombiner {
   struct Req {
     bm_ctx* h;
@@ -1602,8 +1607,12 @@ void spmm_combined(bm_ctx& h, bool csr, const float* vals, const Tall& X, const 
   c.pending.push_back({&h, csr, vals, X, Out, gamma});
   ++c.products;
   const uint64_t g = c.gen;
-  if ((int)c.pending.size() == c.live) c.launch_all();
-  else c.cv.wait(lk, [&] { return c.gen != g; });
+  if ((int)c.pending.size() == c.live) {
+    c.launch_all();
+  } else if (!c.cv.wait_for(lk, std::chrono::microseconds(kCombineWaitUs), [&] { return c.gen != g; })) {
+    // waited long enough for the others: launch what has arrived
+    c.launch_all();
+  }
   if (c.fail != BM_OK) throw Error{c.fail, c.fail_msg};
   // before the next generation can re-record it (that needs this thread back)
   BM_CUDA(cudaStreamWaitEvent(h.stream, c.done, 0));

@@ -45,13 +45,14 @@ void gemm_dev(bm_ctx& h, const Tall& A, const float* C, int ldc, const Tall& Y, 
 // Shared launches of the q-wide residual SpMMs of several handles' PG steps,
 // each running on its own host thread and stream (bm_batch_prox_step).  While
 // h.comb is set, spmm_dev hands its product to the combiner and waits: when
-// every participant still inside its PG step has handed one in, the last to
-// arrive launches them all as batched passes over the concatenated segment
-// lists (one launch per orientation, row width and layout) on the
-// combiner's stream, ordered after each participant's earlier work, and each
-// participant's stream then waits for them.  A participant that finishes its
-// PG step calls spmm_combiner_leave.  The products are the same, bit for
-// bit, as those of separate launches.
+// every participant still inside its PG step has handed one in (or the
+// first waiting product has waited 100 us), the products that have arrived
+// run as batched passes over the concatenated segment lists (one launch per
+// orientation, row width and layout) on the combiner's stream, ordered after
+// each participant's earlier work, and each participant's stream then waits
+// for them.  A participant that finishes its PG step calls
+// spmm_combiner_leave.  The products are the same, bit for bit, as those of
+// separate launches.
 SpmmCombiner* spmm_combiner_create(int participants_max);
 void spmm_combiner_destroy(SpmmCombiner* c);
 void spmm_combiner_begin(SpmmCombiner* c, int participants);
