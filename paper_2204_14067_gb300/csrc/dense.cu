@@ -1112,7 +1112,8 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_eig(const double* __rest
         pp_[tid] = p;
         qq_[tid] = q;
       }
-      __syncthreads();
+      // a round in which no pair rotates leaves A and V as they are
+      if (!__syncthreads_or(tid < half && sn_[tid] != (T)0)) continue;
       // rows p, q of A: a warp per pair, lanes along the row
       const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
       for (int k = warp; k < half; k += nwarp) {
