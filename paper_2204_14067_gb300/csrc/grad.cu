@@ -32,10 +32,21 @@ __global__ void k_fixup(const int32_t* __restrict__ mrow, const int32_t* __restr
     const int c = (int)(t - q * ld);
     const int i = mrow[q];
     const int64_t f = mfirst[q];
-    float s = 0.f;
-    for (int u = 0; u < mcount[q]; ++u) s += partial[(f + u) * ld + c];
+    const int cnt = mcount[q];
+    // four running sums over the partials in segment order (u mod 4), added
+    // in a fixed order: deterministic, and four loads in flight
+    const float* pp = partial + f * ld + c;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int u = 0;
+    for (; u + 3 < cnt; u += 4) {
+      s0 += pp[(int64_t)u * ld];
+      s1 += pp[(int64_t)(u + 1) * ld];
+      s2 += pp[(int64_t)(u + 2) * ld];
+      s3 += pp[(int64_t)(u + 3) * ld];
+    }
+    for (; u < cnt; ++u) s0 += pp[(int64_t)u * ld];
     const int64_t o = (int64_t)i * ld + c;
-    out[o] = fmaf(lam, own[o], s);
+    out[o] = fmaf(lam, own[o], (s0 + s1) + (s2 + s3));
   }
 }
 
@@ -43,9 +54,16 @@ __global__ void k_fixup(const int32_t* __restrict__ mrow, const int32_t* __restr
 __global__ void k_sum_double(const double* __restrict__ x, int64_t n, int stride, int comp,
                              double* __restrict__ out) {
   __shared__ double sh[1024];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i * stride + comp];
-  sh[threadIdx.x] = s;
+  // two running sums per thread (loads in flight), added in a fixed order
+  double s = 0.0, t = 0.0;
+  const int64_t b = blockDim.x;
+  int64_t i = threadIdx.x;
+  for (; i + b < n; i += 2 * b) {
+    s += x[i * stride + comp];
+    t += x[(i + b) * stride + comp];
+  }
+  if (i < n) s += x[i * stride + comp];
+  sh[threadIdx.x] = s + t;
   __syncthreads();
   for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
@@ -148,6 +166,14 @@ void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
 
 }  // namespace
 
+// sum x_i y_i into out (device), without waiting; part: kDotBlocks doubles
+void dot_async(bm_ctx& h, const float* x, const float* y, int64_t count, double* part, double* out) {
+  k_dot_partial<<<kDotBlocks, kDotThreads, 0, h.stream>>>(x, y, count / 4, part);
+  BM_CHECK_LAUNCH();
+  k_sum_double<<<1, 1024, 0, h.stream>>>(part, kDotBlocks, 1, 0, out);
+  BM_CHECK_LAUNCH();
+}
+
 double dot_dev(bm_ctx& h, const float* x, const float* y, int64_t count) {
   double* part = h.sc.red.get();
   double* out = h.sc.scal.get();
@@ -186,10 +212,16 @@ LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r) {
   k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, pass_segs(ix, kPassGradCsr).nseg, 1, 0, h.sc.scal.get() + 1);
   BM_CHECK_LAUNCH();
   if (want_grad) run_pass(h, false, false, nullptr);
-  BM_CUDA(cudaMemcpyAsync(&o.f, h.sc.scal.get() + 1, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+  // ||W||^2 and ||H||^2 on the same stream, then one read-back of the three sums
+  double* sc = h.sc.scal.get();
+  dot_async(h, h.W.get(), h.W.get(), ix.m * h.ld, h.sc.red.get(), sc + 12);
+  dot_async(h, h.H.get(), h.H.get(), ix.n * h.ld, h.sc.red.get() + kDotBlocks, sc + 13);
+  double v[13];
+  BM_CUDA(cudaMemcpyAsync(v, sc + 1, sizeof(v), cudaMemcpyDeviceToHost, h.stream));
   BM_CUDA(cudaStreamSynchronize(h.stream));
-  o.nW2 = dot_dev(h, h.W.get(), h.W.get(), ix.m * h.ld);
-  o.nH2 = dot_dev(h, h.H.get(), h.H.get(), ix.n * h.ld);
+  o.f = v[0];
+  o.nW2 = v[11];
+  o.nH2 = v[12];
   return o;
 }
 
