@@ -374,6 +374,12 @@ void bm_destroy(bm_handle h) {
   h->bb = nullptr;
   bcd_destroy(h->bcd);
   h->bcd = nullptr;
+  if (h->side_stream) {
+    cudaStreamSynchronize(h->side_stream);
+    cudaStreamDestroy(h->side_stream);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
   cudaStream_t own = h->own_stream;
   delete h;
   if (own) cudaStreamDestroy(own);

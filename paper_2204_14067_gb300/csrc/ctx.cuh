@@ -123,6 +123,8 @@ struct bm_ctx {
   bm_options opt{};
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
+  cudaStream_t side_stream = nullptr;         // work that overlaps the sparse passes (created on first use)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int device = 0;
 
   int k = 0;                     // current rank

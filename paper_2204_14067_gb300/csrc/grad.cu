@@ -166,11 +166,11 @@ void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
 
 }  // namespace
 
-// sum x_i y_i into out (device), without waiting; part: kDotBlocks doubles
-void dot_async(bm_ctx& h, const float* x, const float* y, int64_t count, double* part, double* out) {
-  k_dot_partial<<<kDotBlocks, kDotThreads, 0, h.stream>>>(x, y, count / 4, part);
+// sum x_i y_i into out (device) on stream st, without waiting; part: kDotBlocks doubles
+void dot_async(cudaStream_t st, const float* x, const float* y, int64_t count, double* part, double* out) {
+  k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(x, y, count / 4, part);
   BM_CHECK_LAUNCH();
-  k_sum_double<<<1, 1024, 0, h.stream>>>(part, kDotBlocks, 1, 0, out);
+  k_sum_double<<<1, 1024, 0, st>>>(part, kDotBlocks, 1, 0, out);
   BM_CHECK_LAUNCH();
 }
 
@@ -208,14 +208,24 @@ LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r) {
   const Index& ix = h.ix;
   LossOut o{0, 0, 0};
   double* fseg = h.sc.fseg.get();
+  double* sc = h.sc.scal.get();
+  // ||W||^2 and ||H||^2 on a side stream, overlapping the passes (they only
+  // read W and H); one read-back of the three sums at the end
+  if (!h.side_stream) {
+    BM_CUDA(cudaStreamCreateWithFlags(&h.side_stream, cudaStreamNonBlocking));
+    BM_CUDA(cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming));
+    BM_CUDA(cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming));
+  }
+  BM_CUDA(cudaEventRecord(h.fork_ev, h.stream));
+  BM_CUDA(cudaStreamWaitEvent(h.side_stream, h.fork_ev, 0));
+  dot_async(h.side_stream, h.W.get(), h.W.get(), ix.m * h.ld, h.sc.red.get(), sc + 12);
+  dot_async(h.side_stream, h.H.get(), h.H.get(), ix.n * h.ld, h.sc.red.get() + kDotBlocks, sc + 13);
+  BM_CUDA(cudaEventRecord(h.join_ev, h.side_stream));
   run_pass(h, true, store_r, fseg);
-  k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, pass_segs(ix, kPassGradCsr).nseg, 1, 0, h.sc.scal.get() + 1);
+  k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, pass_segs(ix, kPassGradCsr).nseg, 1, 0, sc + 1);
   BM_CHECK_LAUNCH();
   if (want_grad) run_pass(h, false, false, nullptr);
-  // ||W||^2 and ||H||^2 on the same stream, then one read-back of the three sums
-  double* sc = h.sc.scal.get();
-  dot_async(h, h.W.get(), h.W.get(), ix.m * h.ld, h.sc.red.get(), sc + 12);
-  dot_async(h, h.H.get(), h.H.get(), ix.n * h.ld, h.sc.red.get() + kDotBlocks, sc + 13);
+  BM_CUDA(cudaStreamWaitEvent(h.stream, h.join_ev, 0));
   double v[13];
   BM_CUDA(cudaMemcpyAsync(v, sc + 1, sizeof(v), cudaMemcpyDeviceToHost, h.stream));
   BM_CUDA(cudaStreamSynchronize(h.stream));
