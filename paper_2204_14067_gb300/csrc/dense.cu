@@ -1387,10 +1387,16 @@ void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, 
   if (!compensated && sym && h.opt.tensor_grams == 1 && gram_tc_dev(h, w, A, B, C, tag)) return;
   const int ng = (a + 7) / 8, nb = (b + 3) / 4;
   const int tiles = ng * nb;
-  const int gy = (tiles + kGramMaxThreads - 1) / kGramMaxThreads;
+  // short blocks (few rows): each thread's chain is (slab rows) x (its 32
+  // products), so the micro-tiles spread over more, smaller blocks and the
+  // slabs shrink to one 32-row tile
+  const bool short_rows = L <= 16 * kGramRows * 64;
+  const int per_block = short_rows ? 128 : kGramMaxThreads;
+  const int gy = (tiles + per_block - 1) / per_block;
   const int threads = (int)(ceil_div(ceil_div(tiles, gy), 32) * 32);
   // about three blocks per SM in total
-  int64_t gx = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 64), (int64_t)3 * num_sms() / gy));
+  int64_t gx = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, short_rows ? kGramRows : 64),
+                                                      std::max<int64_t>(1, (int64_t)3 * num_sms() / gy)));
   const int64_t slab = ceil_div(ceil_div(L, gx), kGramRows) * kGramRows;
   gx = ceil_div(L, slab);
   static_assert(sizeof(double) == sizeof(float2), "FP32-pair partials share the FP64 scratch");
@@ -1681,11 +1687,13 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
     double* S2 = T1 + (size_t)n * n;
     double* V = S2 + (size_t)n * n;
     sym_eig_dev(h, w, S, n, evals, V0, kEigFast);
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n * n, 256), (int64_t)num_sms() * 4));
-    BM_LAUNCH(h, "eig_rotate", k_small_mm_tn<<<g, 256, 0, h.stream>>>(V0, V0, S2, n));
-    BM_LAUNCH(h, "eig_rotate", k_newton_schulz<<<g, 256, 0, h.stream>>>(V0, S2, V, n));
-    BM_LAUNCH(h, "eig_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(S, V, T1, n, n, n, 0));
-    BM_LAUNCH(h, "eig_rotate", k_small_mm_tn<<<g, 256, 0, h.stream>>>(V, T1, S2, n));
+    // one output per thread, 64-thread blocks: n^2 outputs spread over many SMs
+    // (FP64 issues slowly on this part)
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n * n, 64), (int64_t)num_sms() * 16));
+    BM_LAUNCH(h, "eig_rotate", k_small_mm_tn<<<g, 64, 0, h.stream>>>(V0, V0, S2, n));
+    BM_LAUNCH(h, "eig_rotate", k_newton_schulz<<<g, 64, 0, h.stream>>>(V0, S2, V, n));
+    BM_LAUNCH(h, "eig_rotate", k_small_mm<<<g, 64, 0, h.stream>>>(S, V, T1, n, n, n, 0));
+    BM_LAUNCH(h, "eig_rotate", k_small_mm_tn<<<g, 64, 0, h.stream>>>(V, T1, S2, n));
     w.status.alloc(1);
     BM_CUDA(cudaMemsetAsync(w.status.get(), 0, sizeof(int), h.stream));
     if (jac64) {
@@ -1699,7 +1707,7 @@ void sym_eig_dev(bm_ctx& h, DenseWork& w, const double* S, int n, double* evals,
       BM_LAUNCH(h, "jacobi_eig_rel",
                 k_jacobi_eig<float><<<1, kJacThreads, smem, h.stream>>>(S2, n, 20, kJacRelTol, evals, T1, w.status.get()));
     }
-    BM_LAUNCH(h, "eig_rotate", k_small_mm<<<g, 256, 0, h.stream>>>(V, T1, evecs, n, n, n, 0));
+    BM_LAUNCH(h, "eig_rotate", k_small_mm<<<g, 64, 0, h.stream>>>(V, T1, evecs, n, n, n, 0));
     int st = 0;
     BM_CUDA(cudaMemcpyAsync(&st, w.status.get(), sizeof(int), cudaMemcpyDeviceToHost, h.stream));
     BM_CUDA(cudaStreamSynchronize(h.stream));
