@@ -32,6 +32,11 @@ __device__ __forceinline__ float comp(const float4& v, int i) { return i == 0 ? 
 // (Ogita-Rump-Oishi Dot2).  Slab partials leave as FP32 pairs.
 constexpr int kGramRows = 32;
 constexpr int kGramMaxThreads = 512;
+// slab blocks per SM of the row split: the compensated Grams' dependent
+// two-sum chains want more resident warps (measured: 10 blocks per SM
+// 0.75 -> 0.62 ms for the 480,189 x 64 symmetric Gram), the plain ones fewer
+constexpr int kGramBlocksPerSmPlain = 3;
+constexpr int kGramBlocksPerSmComp = 10;
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -51,9 +56,28 @@ __global__ void __launch_bounds__(kGramMaxThreads) k_gram(const float* __restric
   const int ng = (a + 7) >> 3, na = 2 * ng, a4 = (a + 3) >> 2, nb = (b + 3) >> 2;
   const int stage = kGramRows * (na + nb);
   const int mt = blockIdx.y * blockDim.x + threadIdx.x;
-  const int ti = mt < ng * nb ? mt / nb : 0, tj = mt < ng * nb ? mt % nb : 0;
-  // symmetric Grams (A = B): micro-tiles strictly below the diagonal are skipped
-  const bool active = mt < ng * nb && !(sym && 8 * ti > 4 * tj + 3);
+  int ti = 0, tj = 0;
+  bool active;
+  if (sym) {
+    // symmetric Grams (A = B): only micro-tiles that reach the diagonal or
+    // above are enumerated, column block by column block
+    int rem = mt;
+    active = false;
+    for (int c = 0; c < nb; ++c) {
+      const int cnt = min(ng, (4 * c + 3) / 8 + 1);
+      if (rem < cnt) {
+        ti = rem;
+        tj = c;
+        active = true;
+        break;
+      }
+      rem -= cnt;
+    }
+  } else {
+    active = mt < ng * nb;
+    ti = active ? mt / nb : 0;
+    tj = active ? mt % nb : 0;
+  }
   float hi[32], lo[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q) hi[q] = 0.f, lo[q] = 0.f;
@@ -1386,7 +1410,11 @@ void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, 
   // two operands dominate at these widths) and stay there
   if (!compensated && sym && h.opt.tensor_grams == 1 && gram_tc_dev(h, w, A, B, C, tag)) return;
   const int ng = (a + 7) / 8, nb = (b + 3) / 4;
-  const int tiles = ng * nb;
+  int tiles = ng * nb;
+  if (sym) {   // the kernel enumerates only the micro-tiles on or above the diagonal
+    tiles = 0;
+    for (int c = 0; c < nb; ++c) tiles += std::min(ng, (4 * c + 3) / 8 + 1);
+  }
   // short blocks (few rows): each thread's chain is (slab rows) x (its 32
   // products), so the micro-tiles spread over more, smaller blocks and the
   // slabs shrink to one 32-row tile
@@ -1394,9 +1422,8 @@ void gram_dev(bm_ctx& h, DenseWork& w, const Tall& A, const Tall& B, double* C, 
   const int per_block = short_rows ? 128 : kGramMaxThreads;
   const int gy = (tiles + per_block - 1) / per_block;
   const int threads = (int)(ceil_div(ceil_div(tiles, gy), 32) * 32);
-  // about three blocks per SM in total
   int64_t gx = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, short_rows ? kGramRows : 64),
-                                                      std::max<int64_t>(1, (int64_t)3 * num_sms() / gy)));
+                                                      std::max<int64_t>(1, (int64_t)(compensated ? kGramBlocksPerSmComp : kGramBlocksPerSmPlain) * num_sms() / gy)));
   const int64_t slab = ceil_div(ceil_div(L, gx), kGramRows) * kGramRows;
   gx = ceil_div(L, slab);
   static_assert(sizeof(double) == sizeof(float2), "FP32-pair partials share the FP64 scratch");
