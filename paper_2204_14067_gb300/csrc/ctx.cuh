@@ -89,6 +89,7 @@ inline bool pass_ws(const Index& ix, int kind) {
 struct Scratch {
   int ld_part = 4;                // row width (floats) the partial buffer is sized for
   DevBuf<float> partial;          // segment partial sums
+  DevBuf<float> partial2;         // those of a pass running beside the first (loss/gradient call)
   DevBuf<double> fseg;            // per-segment loss partials
   DevBuf<double> red;             // block partials of dense reductions
   DevBuf<double> scal;            // small device scalars

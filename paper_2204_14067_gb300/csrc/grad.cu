@@ -123,7 +123,7 @@ __global__ void k_xpby(float* __restrict__ y, const float* __restrict__ x, float
 }
 
 
-void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
+void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg, float* partial = nullptr) {
   const Index& ix = h.ix;
   const Segs& sg = pass_segs(ix, csr ? kPassGradCsr : kPassGradCsc);
   PipeArgs a{};
@@ -143,7 +143,7 @@ void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
   a.lam = (float)h.lambda;
   a.out = csr ? h.gW.get() : h.gH.get();
   a.ld_out = h.ld;
-  a.partial = h.sc.partial.get();
+  a.partial = partial ? partial : h.sc.partial.get();
   a.ld_part = h.ld;
   a.fseg = fseg;
   a.r_out = (store_r && csr) ? h.r_csr.get() : nullptr;
@@ -158,9 +158,9 @@ void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg) {
   if (sg.nmulti) {
     const int64_t work = sg.nmulti * h.ld;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), num_sms() * 8));
-    BM_LAUNCH(h, "grad_fixup",
+    BM_LAUNCH(h, csr ? "grad_fixup" : "grad_fixup_csc",
               k_fixup<<<grid, 256, 0, h.stream>>>(sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(), sg.nmulti,
-                                                  h.sc.partial.get(), a.o0, h.ld, a.lam, a.out));
+                                                  a.partial, a.o0, h.ld, a.lam, a.out));
   }
 }
 
@@ -216,15 +216,30 @@ LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r) {
     BM_CUDA(cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming));
     BM_CUDA(cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming));
   }
+  ensure_bf16(h);   // the BF16 copies both passes may gather, before the fork
   BM_CUDA(cudaEventRecord(h.fork_ev, h.stream));
   BM_CUDA(cudaStreamWaitEvent(h.side_stream, h.fork_ev, 0));
   dot_async(h.side_stream, h.W.get(), h.W.get(), ix.m * h.ld, h.sc.red.get(), sc + 12);
   dot_async(h.side_stream, h.H.get(), h.H.get(), ix.n * h.ld, h.sc.red.get() + kDotBlocks, sc + 13);
+  if (want_grad) {
+    // the column pass beside the row pass (they share only read-only inputs;
+    // its split rows use their own partial buffer): the passes' tails overlap
+    const Segs& sc2 = pass_segs(ix, kPassGradCsc);
+    h.sc.partial2.alloc((size_t)std::max<int64_t>(1, sc2.nslots) * h.ld);
+    cudaStream_t main = h.stream;
+    h.stream = h.side_stream;
+    try {
+      run_pass(h, false, false, nullptr, h.sc.partial2.get());
+    } catch (...) {
+      h.stream = main;
+      throw;
+    }
+    h.stream = main;
+  }
   BM_CUDA(cudaEventRecord(h.join_ev, h.side_stream));
   run_pass(h, true, store_r, fseg);
   k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, pass_segs(ix, kPassGradCsr).nseg, 1, 0, sc + 1);
   BM_CHECK_LAUNCH();
-  if (want_grad) run_pass(h, false, false, nullptr);
   BM_CUDA(cudaStreamWaitEvent(h.stream, h.join_ev, 0));
   double v[13];
   BM_CUDA(cudaMemcpyAsync(v, sc + 1, sizeof(v), cudaMemcpyDeviceToHost, h.stream));
