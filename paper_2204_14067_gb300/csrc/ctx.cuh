@@ -206,6 +206,18 @@ struct LossOut {
 // f, gradients (written to h.gW/h.gH when want_grad), residual stored in
 // h.r_csr / h.r_csc when store_r.  Stream-ordered; returns after a sync.
 LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r);
+// Work beside the handle's stream: side_fork makes the side stream (created
+// on first use) wait for the handle's stream so far; launches issued while an
+// OnSideStream lives go to the side stream; side_join makes the handle's
+// stream wait for everything issued on the side stream before it.
+void side_fork(bm_ctx& h);
+void side_join(bm_ctx& h);
+struct OnSideStream {
+  bm_ctx& h;
+  cudaStream_t main;
+  explicit OnSideStream(bm_ctx& hh) : h(hh), main(hh.stream) { h.stream = h.side_stream; }
+  ~OnSideStream() { h.stream = main; }
+};
 // BF16 copy of a row-major block (rows x ld floats -> rows x ldb bfloat16, padded with 0)
 void to_bf16_dev(bm_ctx& h, const float* src, int64_t rows, int ld, uint16_t* dst, int ldb);
 // Refresh the BF16 copies of W and H if they are stale.
