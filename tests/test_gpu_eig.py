@@ -1,5 +1,6 @@
 """The one-block symmetric eigensolver (bm_sym_eig) in its three modes against
-LAPACK's eigh in FP64, on the spectra the PG step produces: random
+LAPACK's eigh in FP64 (sizes on both sides of the divide-and-conquer
+range 24 ... 150 of mode 0), on the spectra the PG step produces: random
 symmetric, graded positive definite (Rayleigh-Ritz matrices of Algorithm 2,
 whose Ritz values span many decades), clustered and rank-deficient Grams
 (Eq. "orth-W"), a diagonal input and a single entry.
@@ -67,7 +68,7 @@ def _check_common(S, ev, V, n):
     assert orth <= 20 * np.sqrt(n) * EPS32, orth
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 16, 65, 130, 200, 256])
+@pytest.mark.parametrize("n", [1, 2, 3, 16, 23, 24, 65, 130, 150, 151, 200, 256])
 @pytest.mark.parametrize("kind", ["random", "graded", "cluster", "deficient", "diagonal"])
 def test_fast_mode_against_eigh(B, n, kind):
     rng = np.random.default_rng(1000 * n + len(kind))
