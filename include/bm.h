@@ -387,8 +387,10 @@ bm_status bm_batch_bm_phase(bm_batch b, int32_t epochs, double* F);
  * and the results are bit for bit those of bm_prox_step.  Handles of any rank
  * may take part.  info (bm_prox_info[count], nullable) receives each
  * handle's result, status (bm_status[count], nullable) each handle's status
- * (a failing handle does not stop the others).  Errors: the first failing
- * handle's status, with its message in bm_batch_last_error.
+ * (a handle whose own step fails leaves and does not stop the others; a
+ * shared launch that fails fails every handle's step still in the batch).
+ * Errors: the first failing handle's status, with its message in
+ * bm_batch_last_error.
  *
  * bm_batch_stats -- the products handed to the shared launches so far and
  * the launches made for them (nullable outputs).

@@ -615,25 +615,41 @@ bm_status bm_batch_prox_step(bm_batch b, double alpha, bm_prox_info* info, bm_st
     for (int p = 0; p < b->count; ++p)
       BM_REQUIRE(!b->hs[p]->comb, BM_ERR_INVALID, "bm_batch_prox_step: a handle is already in a batched PG step");
     if (!b->comb) b->comb = spmm_combiner_create(b->count);
-    spmm_combiner_begin(b->comb, b->count);
-    for (int p = 0; p < b->count; ++p) b->hs[p]->comb = b->comb;
     int dev = 0;
     BM_CUDA(cudaGetDevice(&dev));
     std::vector<bm_status> st(b->count, BM_OK);
     std::vector<bm_prox_info> tmp(b->count);
+    spmm_combiner_begin(b->comb, b->count);
     {
+      // the handles leave the batched step however it ends
+      struct Release {
+        bm_batch_ctx* b;
+        ~Release() {
+          for (int p = 0; p < b->count; ++p) b->hs[p]->comb = nullptr;
+        }
+      } release{b};
+      for (int p = 0; p < b->count; ++p) b->hs[p]->comb = b->comb;
       // one host thread per handle: each runs its PG step on its own stream,
       // the residual SpMMs meet in the combiner
       std::vector<std::thread> th;
-      for (int p = 0; p < b->count; ++p)
-        th.emplace_back([&, p] {
-          cudaSetDevice(dev);
-          st[p] = bm_prox_step(b->hs[p], alpha, info ? &info[p] : &tmp[p]);
+      th.reserve(b->count);
+      for (int p = 0; p < b->count; ++p) {
+        try {
+          th.emplace_back([&, p] {
+            cudaSetDevice(dev);
+            st[p] = bm_prox_step(b->hs[p], alpha, info ? &info[p] : &tmp[p]);
+            spmm_combiner_leave(b->comb);
+          });
+        } catch (...) {
+          // no thread for this handle: it leaves at once, so that the others
+          // do not wait for its products
+          b->hs[p]->err = "bm_batch_prox_step: could not start a host thread";
+          st[p] = BM_ERR_INVALID;
           spmm_combiner_leave(b->comb);
-        });
+        }
+      }
       for (auto& t : th) t.join();
     }
-    for (int p = 0; p < b->count; ++p) b->hs[p]->comb = nullptr;
     if (status)
       for (int p = 0; p < b->count; ++p) status[p] = st[p];
     for (int p = 0; p < b->count; ++p)

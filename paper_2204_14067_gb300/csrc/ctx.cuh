@@ -209,9 +209,19 @@ LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r);
 // Work beside the handle's stream: side_fork makes the side stream (created
 // on first use) wait for the handle's stream so far; launches issued while an
 // OnSideStream lives go to the side stream; side_join makes the handle's
-// stream wait for everything issued on the side stream before it.
+// stream wait for everything issued on the side stream before it.  A
+// SideScope forks on construction and joins when it goes out of scope, also
+// when an exception leaves it, so that no later work on the handle's stream
+// can overtake side-stream work of a failed call.
 void side_fork(bm_ctx& h);
-void side_join(bm_ctx& h);
+void side_join(bm_ctx& h) noexcept;
+struct SideScope {
+  bm_ctx& h;
+  explicit SideScope(bm_ctx& hh) : h(hh) { side_fork(h); }
+  ~SideScope() { side_join(h); }
+  SideScope(const SideScope&) = delete;
+  SideScope& operator=(const SideScope&) = delete;
+};
 struct OnSideStream {
   bm_ctx& h;
   cudaStream_t main;

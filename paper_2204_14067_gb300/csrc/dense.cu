@@ -1491,102 +1491,111 @@ struct SpmmCombiner {
   DevBuf<PipeArgs> args_d;
   DevBuf<int64_t> prefix_d;
   int cap = 0;                             // slices the device tables hold
-  bm_status fail = BM_OK;
+  bm_status fail = BM_OK;   // sticky until spmm_combiner_begin: a failed launch fails every later product
   std::string fail_msg;
   int64_t launches = 0;   // batched SpMM launches
   int64_t products = 0;   // products handed in
 
-  // Launch every pending product (called with mu held by the last arrival).
+  // Launch every pending product (called with mu held, by the last arrival or
+  // by a product that waited long enough).  After a failed launch nothing is
+  // launched again in this batched step: a participant woken late then reads
+  // the failure, never a later generation's success, as its own.
   void launch_all() {
-    fail = BM_OK;
-    try {
-      for (const Req& r : pending) BM_CUDA(cudaStreamWaitEvent(st, ready.at(r.h), 0));
-      struct Slice {
-        const Req* r;
-        PipeArgs a;
-        bool ws;
-        int cols;
-        const Segs* sg;
-      };
-      std::vector<Slice> sl;
-      for (const Req& r : pending) {
-        const Index& ix = r.h->ix;
-        const int kind = r.csr ? kPassSpmmCsr : kPassSpmmCsc;
-        const Segs& sg = pass_segs(ix, kind);
-        for (int c0 = 0; c0 < r.X.cols; c0 += kSpmmCols) {
-          const int cols = std::min(kSpmmCols, r.X.cols - c0);
-          PipeArgs a{};
-          a.seg_row = sg.row.get();
-          a.seg_beg = sg.beg.get();
-          a.seg_end = sg.end.get();
-          a.seg_slot = sg.slot.get();
-          a.nseg = sg.nseg;
-          a.idx = r.csr ? ix.col.get() : ix.row.get();
-          a.scal = r.vals;
-          a.g0 = r.X.p + c0;
-          a.ld = r.X.ld;
-          a.nchunk = (cols + 3) / 4;
-          a.gamma = r.gamma;
-          a.out = r.Out.p + c0;
-          a.ld_out = r.Out.ld;
-          a.partial = r.h->sc.partial.get();
-          a.ld_part = 4 * a.nchunk;
-          BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ld_part <= (int64_t)r.h->sc.partial.n,
-                     BM_ERR_INVALID, "spmm: partial buffer too small");
-          sl.push_back({&r, a, pass_ws(ix, kind), cols, &sg});
-        }
+    if (fail == BM_OK) {
+      try {
+        launch_pending();
+      } catch (const Error& e) {
+        fail = e.code;
+        fail_msg = e.msg;
+      } catch (...) {
+        fail = BM_ERR_CUDA;
+        fail_msg = "spmm combiner: launch failed";
       }
-      // one launch per (orientation, row width, layout)
-      std::stable_sort(sl.begin(), sl.end(), [](const Slice& x, const Slice& y) {
-        return std::make_tuple(x.r->csr, x.a.nchunk, x.ws) < std::make_tuple(y.r->csr, y.a.nchunk, y.ws);
-      });
-      if ((int)sl.size() > cap) throw Error{BM_ERR_INVALID, "spmm combiner: more products than the tables hold"};
-      std::vector<PipeArgs> A;
-      std::vector<int64_t> P;
-      size_t off = 0, poff = 0;
-      for (size_t g0 = 0; g0 < sl.size();) {
-        size_t g1 = g0 + 1;
-        while (g1 < sl.size() && sl[g1].r->csr == sl[g0].r->csr && sl[g1].a.nchunk == sl[g0].a.nchunk &&
-               sl[g1].ws == sl[g0].ws)
-          ++g1;
-        A.clear();
-        P.assign(1, 0);
-        for (size_t i = g0; i < g1; ++i) {
-          A.push_back(sl[i].a);
-          P.push_back(P.back() + sl[i].a.nseg);
-        }
-        // pageable sources: the copies are staged before the calls return
-        BM_CUDA(cudaMemcpyAsync(args_d.get() + off, A.data(), A.size() * sizeof(PipeArgs), cudaMemcpyHostToDevice,
-                                st));
-        BM_CUDA(cudaMemcpyAsync(prefix_d.get() + poff, P.data(), P.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                                st));
-        launch_direct_batch<1>(args_d.get() + off, prefix_d.get() + poff, (int)A.size(), P.back(),
-                               sl[g0].a.nchunk, false, sl[g0].ws, st);
-        BM_CHECK_LAUNCH();
-        ++launches;
-        off += A.size();
-        poff += P.size();
-        g0 = g1;
-      }
-      for (const Slice& x : sl) {
-        const Segs& sg = *x.sg;
-        if (!sg.nmulti) continue;
-        k_spmm_fixup<<<grid1(sg.nmulti * x.cols), 256, 0, st>>>(sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(),
-                                                                 sg.nmulti, x.a.partial, x.a.ld_part, x.cols,
-                                                                 x.a.gamma, x.a.out, x.a.ld_out);
-        BM_CHECK_LAUNCH();
-      }
-      BM_CUDA(cudaEventRecord(done, st));
-    } catch (const Error& e) {
-      fail = e.code;
-      fail_msg = e.msg;
-    } catch (...) {
-      fail = BM_ERR_CUDA;
-      fail_msg = "spmm combiner: launch failed";
     }
     pending.clear();
     ++gen;
     cv.notify_all();
+  }
+
+  // Batched launches of the pending products on the combiner's stream (throws).
+  void launch_pending() {
+    for (const Req& r : pending) BM_CUDA(cudaStreamWaitEvent(st, ready.at(r.h), 0));
+    struct Slice {
+      const Req* r;
+      PipeArgs a;
+      bool ws;
+      int cols;
+      const Segs* sg;
+    };
+    std::vector<Slice> sl;
+    for (const Req& r : pending) {
+      const Index& ix = r.h->ix;
+      const int kind = r.csr ? kPassSpmmCsr : kPassSpmmCsc;
+      const Segs& sg = pass_segs(ix, kind);
+      for (int c0 = 0; c0 < r.X.cols; c0 += kSpmmCols) {
+        const int cols = std::min(kSpmmCols, r.X.cols - c0);
+        PipeArgs a{};
+        a.seg_row = sg.row.get();
+        a.seg_beg = sg.beg.get();
+        a.seg_end = sg.end.get();
+        a.seg_slot = sg.slot.get();
+        a.nseg = sg.nseg;
+        a.idx = r.csr ? ix.col.get() : ix.row.get();
+        a.scal = r.vals;
+        a.g0 = r.X.p + c0;
+        a.ld = r.X.ld;
+        a.nchunk = (cols + 3) / 4;
+        a.gamma = r.gamma;
+        a.out = r.Out.p + c0;
+        a.ld_out = r.Out.ld;
+        a.partial = r.h->sc.partial.get();
+        a.ld_part = 4 * a.nchunk;
+        BM_REQUIRE((int64_t)std::max<int64_t>(1, sg.nslots) * a.ld_part <= (int64_t)r.h->sc.partial.n,
+                   BM_ERR_INVALID, "spmm: partial buffer too small");
+        sl.push_back({&r, a, pass_ws(ix, kind), cols, &sg});
+      }
+    }
+    // one launch per (orientation, row width, layout)
+    std::stable_sort(sl.begin(), sl.end(), [](const Slice& x, const Slice& y) {
+      return std::make_tuple(x.r->csr, x.a.nchunk, x.ws) < std::make_tuple(y.r->csr, y.a.nchunk, y.ws);
+    });
+    if ((int)sl.size() > cap) throw Error{BM_ERR_INVALID, "spmm combiner: more products than the tables hold"};
+    std::vector<PipeArgs> A;
+    std::vector<int64_t> P;
+    size_t off = 0, poff = 0;
+    for (size_t g0 = 0; g0 < sl.size();) {
+      size_t g1 = g0 + 1;
+      while (g1 < sl.size() && sl[g1].r->csr == sl[g0].r->csr && sl[g1].a.nchunk == sl[g0].a.nchunk &&
+             sl[g1].ws == sl[g0].ws)
+        ++g1;
+      A.clear();
+      P.assign(1, 0);
+      for (size_t i = g0; i < g1; ++i) {
+        A.push_back(sl[i].a);
+        P.push_back(P.back() + sl[i].a.nseg);
+      }
+      // pageable sources: the copies are staged before the calls return
+      BM_CUDA(cudaMemcpyAsync(args_d.get() + off, A.data(), A.size() * sizeof(PipeArgs), cudaMemcpyHostToDevice,
+                              st));
+      BM_CUDA(cudaMemcpyAsync(prefix_d.get() + poff, P.data(), P.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              st));
+      launch_direct_batch<1>(args_d.get() + off, prefix_d.get() + poff, (int)A.size(), P.back(),
+                             sl[g0].a.nchunk, false, sl[g0].ws, st);
+      BM_CHECK_LAUNCH();
+      ++launches;
+      off += A.size();
+      poff += P.size();
+      g0 = g1;
+    }
+    for (const Slice& x : sl) {
+      const Segs& sg = *x.sg;
+      if (!sg.nmulti) continue;
+      k_spmm_fixup<<<grid1(sg.nmulti * x.cols), 256, 0, st>>>(sg.mrow.get(), sg.mfirst.get(), sg.mcount.get(),
+                                                               sg.nmulti, x.a.partial, x.a.ld_part, x.cols,
+                                                               x.a.gamma, x.a.out, x.a.ld_out);
+      BM_CHECK_LAUNCH();
+    }
+    BM_CUDA(cudaEventRecord(done, st));
   }
 };
 
@@ -1616,6 +1625,8 @@ void spmm_combiner_begin(SpmmCombiner* c, int participants) {
   std::lock_guard<std::mutex> lk(c->mu);
   c->live = participants;
   c->pending.clear();
+  c->fail = BM_OK;
+  c->fail_msg.clear();
 }
 
 void spmm_combiner_leave(SpmmCombiner* c) {
@@ -1648,7 +1659,9 @@ void spmm_combined(bm_ctx& h, bool csr, const float* vals, const Tall& X, const 
     c.launch_all();
   }
   if (c.fail != BM_OK) throw Error{c.fail, c.fail_msg};
-  // before the next generation can re-record it (that needs this thread back)
+  // A later generation may already have re-recorded `done` (one launched by a
+  // product that waited long enough); that record follows this generation's
+  // launches on the combiner's stream, so waiting for it covers them too.
   BM_CUDA(cudaStreamWaitEvent(h.stream, c.done, 0));
 }
 }  // namespace

@@ -167,18 +167,18 @@ void run_pass(bm_ctx& h, bool csr, bool store_r, double* fseg, float* partial = 
 }  // namespace
 
 void side_fork(bm_ctx& h) {
-  if (!h.side_stream) {
-    BM_CUDA(cudaStreamCreateWithFlags(&h.side_stream, cudaStreamNonBlocking));
-    BM_CUDA(cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming));
-    BM_CUDA(cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming));
-  }
+  if (!h.fork_ev) BM_CUDA(cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming));
+  if (!h.join_ev) BM_CUDA(cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming));
+  if (!h.side_stream) BM_CUDA(cudaStreamCreateWithFlags(&h.side_stream, cudaStreamNonBlocking));
   BM_CUDA(cudaEventRecord(h.fork_ev, h.stream));
   BM_CUDA(cudaStreamWaitEvent(h.side_stream, h.fork_ev, 0));
 }
 
-void side_join(bm_ctx& h) {
-  BM_CUDA(cudaEventRecord(h.join_ev, h.side_stream));
-  BM_CUDA(cudaStreamWaitEvent(h.stream, h.join_ev, 0));
+// A failure here leaves the error pending in the context: the next call on
+// the handle's stream (the result read-back) reports it.
+void side_join(bm_ctx& h) noexcept {
+  if (!h.side_stream) return;
+  if (cudaEventRecord(h.join_ev, h.side_stream) == cudaSuccess) cudaStreamWaitEvent(h.stream, h.join_ev, 0);
 }
 
 // sum x_i y_i into out (device) on stream st, without waiting; part: kDotBlocks doubles
@@ -227,23 +227,25 @@ LossOut loss_grad_dev(bm_ctx& h, bool want_grad, bool store_r) {
   // ||W||^2 and ||H||^2 on the side stream, overlapping the passes (they only
   // read W and H); one read-back of the three sums at the end
   ensure_bf16(h);   // the BF16 copies both passes may gather, before the fork
-  side_fork(h);
   if (want_grad) {
     const Segs& sc2 = pass_segs(ix, kPassGradCsc);
     h.sc.partial2.alloc((size_t)std::max<int64_t>(1, sc2.nslots) * h.ld);
   }
   {
-    OnSideStream side(h);
-    dot_async(h.stream, h.W.get(), h.W.get(), ix.m * h.ld, h.sc.red.get(), sc + 12);
-    dot_async(h.stream, h.H.get(), h.H.get(), ix.n * h.ld, h.sc.red.get() + kDotBlocks, sc + 13);
-    // the column pass beside the row pass (they share only read-only inputs;
-    // its split rows use their own partial buffer): the passes' tails overlap
-    if (want_grad) run_pass(h, false, false, nullptr, h.sc.partial2.get());
-  }
-  run_pass(h, true, store_r, fseg);
-  k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, pass_segs(ix, kPassGradCsr).nseg, 1, 0, sc + 1);
-  BM_CHECK_LAUNCH();
-  side_join(h);
+    SideScope fork(h);
+    {
+      OnSideStream side(h);
+      dot_async(h.stream, h.W.get(), h.W.get(), ix.m * h.ld, h.sc.red.get(), sc + 12);
+      dot_async(h.stream, h.H.get(), h.H.get(), ix.n * h.ld, h.sc.red.get() + kDotBlocks, sc + 13);
+      // the column pass beside the row pass (they share only read-only
+      // inputs; its split rows use their own partial buffer): the passes'
+      // tails overlap
+      if (want_grad) run_pass(h, false, false, nullptr, h.sc.partial2.get());
+    }
+    run_pass(h, true, store_r, fseg);
+    k_sum_double<<<1, 1024, 0, h.stream>>>(fseg, pass_segs(ix, kPassGradCsr).nseg, 1, 0, sc + 1);
+    BM_CHECK_LAUNCH();
+  }   // the handle's stream waits for the side stream here
   double v[13];
   BM_CUDA(cudaMemcpyAsync(v, sc + 1, sizeof(v), cudaMemcpyDeviceToHost, h.stream));
   BM_CUDA(cudaStreamSynchronize(h.stream));
