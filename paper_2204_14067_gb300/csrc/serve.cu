@@ -109,11 +109,15 @@ void finish(bm_server_ctx& s, Active& a, bm_status st) {
   bool keep = false;
   if (s.o.keep_factors && st == BM_OK && a.h) {
     kf.k = k;
-    kf.W.resize((size_t)a.req.m * k);
-    kf.H.resize((size_t)a.req.n * k);
-    int32_t kk = 0;
-    if (bm_get_factors(a.h, &kk, kf.W.data(), kf.H.data()) == BM_OK && kk == k) keep = true;
-    else r.status = BM_ERR_CUDA;
+    try {
+      kf.W.resize((size_t)a.req.m * k);
+      kf.H.resize((size_t)a.req.n * k);
+      int32_t kk = 0;
+      if (bm_get_factors(a.h, &kk, kf.W.data(), kf.H.data()) == BM_OK && kk == k) keep = true;
+      else r.status = BM_ERR_CUDA;
+    } catch (...) {
+      r.status = BM_ERR_OOM;   // no host memory for the kept factors
+    }
   }
   if (a.h) bm_destroy(a.h);
   a.h = nullptr;
@@ -220,27 +224,35 @@ void run_batched(bm_server_ctx& s) {
       if (st != BM_OK)
         for (size_t i : in_batch) sts[i] = st;
     }
-    // PG steps concurrently, each solve on its own stream
+    // PG steps concurrently, each solve on its own stream; the server thread
+    // is one of the workers (a worker thread that cannot be started leaves
+    // its share to the others)
     std::atomic<size_t> next{0};
+    auto work = [&] {
+      cudaSetDevice(s.device);
+      for (size_t i = next++; i < act.size(); i = next++) {
+        if (sts[i] != BM_OK) continue;
+        bm_prox_info pi{};
+        sts[i] = bm_prox_step(act[i].h, 0.0, &pi);
+        act[i].F_prev = act[i].F;
+        act[i].F = pi.F;
+        act[i].outer++;
+        // BF16 gathers: the final iterations run in FP32 once progress stalls
+        if (std::isfinite(act[i].F_prev) && act[i].h->opt.precision == 1 && !act[i].h->refine &&
+            (std::fabs(act[i].F_prev - act[i].F) / (1.0 + std::fabs(act[i].F_prev)) < 3e-3 ||
+             act[i].F >= act[i].F_prev))
+          act[i].h->refine = true;
+      }
+    };
     std::vector<std::thread> pool;
-    for (int w = 0; w < std::min<int>(nw, (int)act.size()); ++w) {
-      pool.emplace_back([&] {
-        cudaSetDevice(s.device);
-        for (size_t i = next++; i < act.size(); i = next++) {
-          if (sts[i] != BM_OK) continue;
-          bm_prox_info pi{};
-          sts[i] = bm_prox_step(act[i].h, 0.0, &pi);
-          act[i].F_prev = act[i].F;
-          act[i].F = pi.F;
-          act[i].outer++;
-          // BF16 gathers: the final iterations run in FP32 once progress stalls
-          if (std::isfinite(act[i].F_prev) && act[i].h->opt.precision == 1 && !act[i].h->refine &&
-              (std::fabs(act[i].F_prev - act[i].F) / (1.0 + std::fabs(act[i].F_prev)) < 3e-3 ||
-               act[i].F >= act[i].F_prev))
-            act[i].h->refine = true;
-        }
-      });
+    for (int w = 1; w < std::min<int>(nw, (int)act.size()); ++w) {
+      try {
+        pool.emplace_back(work);
+      } catch (...) {
+        break;
+      }
     }
+    work();
     for (auto& t : pool) t.join();
     // retire finished solves.  A batch must not outlive its handles: when a
     // member retires the batch is destroyed first (a later bm_create may
@@ -278,15 +290,22 @@ bm_status bm_server_create(const bm_server_opts* o, bm_server* out) {
     g_server_error = "bm_server_create: max_active, max_outer >= 1, precision and keep_factors 0 or 1 required";
     return BM_ERR_INVALID;
   }
-  bm_server_ctx* s = new bm_server_ctx();
-  s->o = *o;
-  s->t0 = Clock::now();
-  cudaGetDevice(&s->device);
-  s->th = std::thread([s] {
-    cudaSetDevice(s->device);
-    if (s->o.batched) run_batched(*s);
-    else run_plain(*s);
-  });
+  bm_server_ctx* s = nullptr;
+  try {
+    s = new bm_server_ctx();
+    s->o = *o;
+    s->t0 = Clock::now();
+    cudaGetDevice(&s->device);
+    s->th = std::thread([s] {
+      cudaSetDevice(s->device);
+      if (s->o.batched) run_batched(*s);
+      else run_plain(*s);
+    });
+  } catch (...) {
+    delete s;
+    g_server_error = "bm_server_create: could not allocate the server or start its thread";
+    return BM_ERR_OOM;
+  }
   *out = s;
   return BM_OK;
 }
@@ -296,15 +315,22 @@ bm_status bm_server_submit(bm_server s, int64_t m, int64_t n, int64_t nnz, const
   if (!s) return BM_ERR_INVALID;
   if (m < 1 || n < 1 || nnz < 0 || (nnz && (!rows || !cols || !vals)) || !(lambda > 0) || k_max < 1 ||
       k_max > std::min<int64_t>(std::min(m, n), 127)) {
+    std::lock_guard<std::mutex> lk(s->mu);
     s->err = "bm_server_submit: invalid request";
     return BM_ERR_INVALID;
   }
   Request r;
   r.m = m;
   r.n = n;
-  r.rows.assign(rows, rows + nnz);
-  r.cols.assign(cols, cols + nnz);
-  r.vals.assign(vals, vals + nnz);
+  try {
+    r.rows.assign(rows, rows + nnz);
+    r.cols.assign(cols, cols + nnz);
+    r.vals.assign(vals, vals + nnz);
+  } catch (...) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "bm_server_submit: no host memory for the request's copy";
+    return BM_ERR_OOM;
+  }
   r.lambda = lambda;
   r.k_max = k_max;
   {
