@@ -42,7 +42,8 @@ Readings (each also in the design notes):
 
 Parity status: pinned by tests/test_oracle_edm_solve.py (Lemma "PiX" through
 projection optimality, the dense exact PG step, the line-search quartic,
-monotone BM phase, and the dense convex optimum of the QSDP).
+monotone BM phase, the BM phase's iterates against the definition of
+Polak-Ribiere+ CG with exact steps, and the dense convex optimum of the QSDP).
 """
 from __future__ import annotations
 

@@ -1,13 +1,15 @@
 """Pins of the distance-geometry QSDP oracle (oracle/edm_oracle.py) against
 facts independent of it: the variational inequality of a projection onto a
 convex set (Lemma "PiX"), dense operators, finite differences, brute-force
-line search, the exact operator norm, the dense exact PG step, and the dense
-convex optimum of the QSDP."""
+line search, the exact operator norm, the dense exact PG step, the definition
+of Polak-Ribiere+ CG with exact steps, and the dense convex optimum of the
+QSDP."""
 import numpy as np
 import pytest
 
 from oracle import bm_oracle as O
 from oracle import edm_oracle as E
+from cg_pin import check_pr_plus
 from synth import self_avoiding_chain
 
 
@@ -70,6 +72,25 @@ def test_gradient_and_line_search_quartic():
     V2, F = E.bm_phase(V, i, j, d, w, lam, 6)
     assert all(b <= a * (1 + 1e-12) + 1e-12 for a, b in zip(F, F[1:]))
     assert np.abs(V2.sum(axis=0)).max() <= 1e-9
+
+
+def test_bm_phase_is_pr_plus_cg_with_exact_steps():
+    """The BM phase's iterates (calls of 1 ... 6 epochs from one centred start)
+    against the definition of Polak-Ribiere+ CG with an exact line search on
+    g(V) = f(V V^T) + lam ||V||^2, by central differences of E.objective and
+    brute-force steps (tests/cg_pin.py).  On this chain one step has a
+    negative Polak-Ribiere ratio (PR+ restarts there) and others tell the
+    Polak-Ribiere ratio from the Fletcher-Reeves one."""
+    n = 10
+    p, i, j, d, w = _chain(n, 3)
+    lam = O.edm_lambda(n, d)
+    V0 = E.center(np.random.default_rng(3).standard_normal((n, 2)))
+    xs = [V0.ravel()]
+    for e in range(1, 7):
+        V, _ = E.bm_phase(V0, i, j, d, w, lam, e)
+        xs.append(V.ravel())
+    restarts, fr_apart = check_pr_plus(xs, lambda v: E.objective(v.reshape(n, 2), i, j, d, w, lam))
+    assert restarts >= 1 and fr_apart >= 1
 
 
 def test_lipschitz_bound_dominates_the_operator_norm():

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import bm_oracle as O
+from cg_pin import check_pr_plus
 from synth import planted_uniform, random_factors
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -256,6 +257,33 @@ def test_bm_phase_nonincreasing():
     st2, trace = O.bm_phase(ix, st, p.lam, 25)
     trace.append(O.objective(ix, st2.W, st2.H, p.lam))
     assert all(b <= a * (1 + 1e-15) for a, b in zip(trace, trace[1:]))
+
+
+@pytest.mark.parametrize("seed, frac", [(22, 0.6), (57, 0.3)])
+def test_bm_phase_is_pr_plus_cg_with_exact_steps(seed, frac):
+    """The BM phase's iterates, rebuilt from calls of 1 ... 6 epochs, against
+    the definition of Polak-Ribiere+ nonlinear CG with an exact line search,
+    by central differences and brute-force steps (tests/cg_pin.py).  Seed 22
+    has steps where the Fletcher-Reeves ratio differs from the Polak-Ribiere
+    one by far more than the tolerance; seed 57 has a step with a negative
+    Polak-Ribiere ratio, where PR+ restarts (beta = 0)."""
+    p = planted_uniform(m=6, n=8, rank=2, frac=frac, noise_sd=0.1, lam=0.5, seed=seed)
+    ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals)
+    W, H = random_factors(ix.m, ix.n, 2, seed=seed + 1, scale=0.5)
+    W, H = W.astype(np.float64), H.astype(np.float64)
+    st = _state_from(W, H, O.Options())
+    E = 6
+    xs = [np.concatenate([W.ravel(), H.ravel()])]
+    for e in range(1, E + 1):
+        st_e, _ = O.bm_phase(ix, st, p.lam, e)
+        xs.append(np.concatenate([st_e.W.ravel(), st_e.H.ravel()]))
+    nw = W.size
+
+    def F(v):
+        return O.objective(ix, v[:nw].reshape(W.shape), v[nw:].reshape(H.shape), p.lam)
+
+    restarts, fr_apart = check_pr_plus(xs, F)
+    assert (restarts if seed == 57 else fr_apart) >= 1
 
 
 # ---------------------------------------------------------------- Algorithm 1
