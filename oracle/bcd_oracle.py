@@ -28,8 +28,9 @@ direction with an exact line search is the reading used here.
 Parity status: pinned by tests/test_oracle_bcd.py (block gradient against
 central finite differences, the line-search quartic against the objective
 along the direction, its minimiser against a brute-force grid, F
-nonincreasing after every block, and full observation reaching the
-closed-form optimum of the factored problem).
+nonincreasing after every block, full observation reaching the closed-form
+optimum of the factored problem, and a sweep rebuilt from central
+differences and brute-force steps in column order).
 """
 from __future__ import annotations
 

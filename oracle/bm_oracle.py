@@ -33,7 +33,9 @@ design notes):
     only requires the non-increase condition, Eq. "nonincrease").
 
 Parity status: every function here is pinned by tests/test_oracle_*.py
-(closed forms, finite differences, brute force, invariants).
+(closed forms, finite differences, brute force, invariants);
+tests/oracle_mutations.py plants plausible mistakes in a copy of this file
+and the other oracles and checks that a pin catches each one.
 """
 from __future__ import annotations
 

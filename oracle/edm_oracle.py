@@ -43,7 +43,10 @@ Readings (each also in the design notes):
 Parity status: pinned by tests/test_oracle_edm_solve.py (Lemma "PiX" through
 projection optimality, the dense exact PG step, the line-search quartic,
 monotone BM phase, the BM phase's iterates against the definition of
-Polak-Ribiere+ CG with exact steps, and the dense convex optimum of the QSDP).
+Polak-Ribiere+ CG with exact steps, the Lipschitz bound exact for disjoint
+pairs, Z + sigma I positive semidefinite where half of sigma is not, the
+rank rule and initial rank of the QSDP experiments, the cycle order and
+alpha = 1/L, and the dense convex optimum of the QSDP).
 """
 from __future__ import annotations
 

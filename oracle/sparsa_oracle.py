@@ -35,8 +35,10 @@ Eq. "back" exactly when delta >= alpha / 2), max_backtracks = 30.
 Parity status: pinned by tests/test_oracle_sparsa.py (Eq. "trace" and the
 nuclear norm against dense evaluations, <dX, dG> against the dense gradient
 difference, the full-observation case alpha_BB = 1, the acceptance tests
-re-evaluated densely, no backtracking when alpha_max <= 1/L, and the
-soft-impute optimum reached by the SpaRSA solve).
+re-evaluated densely with the flag naming the test that held and the trial
+one reduction earlier failing both, alpha_BB from the two points where the
+PG steps were taken and the first step's fixed alpha, no backtracking when
+alpha_max <= 1/L, and the soft-impute optimum reached by the SpaRSA solve).
 """
 from __future__ import annotations
 

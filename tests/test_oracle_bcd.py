@@ -1,10 +1,12 @@
 """Pins of the column-block coordinate descent oracle (oracle/bcd_oracle.py):
 the block gradient against central finite differences, the line-search
 quartic against the objective along the direction, its minimiser against a
-brute-force grid, F nonincreasing block by block, and full observation
-reaching the closed-form optimum of the factored problem."""
+brute-force grid, F nonincreasing block by block, full observation
+reaching the closed-form optimum of the factored problem, and a whole sweep
+rebuilt from central differences and brute-force steps in column order."""
 import numpy as np
 
+from cg_pin import fd_gradient, global_step
 from oracle import bcd_oracle as C
 from oracle import bm_oracle as O
 from synth import planted_uniform
@@ -82,3 +84,33 @@ def test_full_observation_reaches_the_closed_form_optimum():
     W, H = rng.standard_normal((ix.m, 3)) * 0.5, rng.standard_normal((ix.n, 3)) * 0.5
     W, H, F = C.bcd_phase(ix, W, H, lam, 3000)
     assert abs(F[-1] - F_star) <= 1e-8 * F_star
+
+
+def test_sweep_is_exact_block_steps_in_column_order():
+    """One sweep rebuilt without the oracle's block machinery: for c = 0, 1,
+    ..., k - 1 in turn, the block gradient of column c of W and H by central
+    differences of the objective, and the exact step along its negative by a
+    brute-force scalar minimisation (tests/cg_pin.py).  Blocks taken in
+    another order reach a different point."""
+    p = planted_uniform(m=6, n=8, rank=2, frac=0.6, noise_sd=0.1, lam=0.5, seed=9)
+    ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals)
+    rng = np.random.default_rng(2)
+    W0, H0 = rng.standard_normal((ix.m, 3)) * 0.5, rng.standard_normal((ix.n, 3)) * 0.5
+    W, H = W0.copy(), H0.copy()
+    for c in range(3):
+        def F(v, c=c, W=W, H=H):
+            W2, H2 = W.copy(), H.copy()
+            W2[:, c], H2[:, c] = v[:ix.m], v[ix.m:]
+            return O.objective(ix, W2, H2, p.lam)
+
+        x = np.concatenate([W[:, c], H[:, c]])
+        d = -fd_gradient(F, x)
+        x = x + global_step(F, x, d) * d
+        W, H = W.copy(), H.copy()
+        W[:, c], H[:, c] = x[:ix.m], x[ix.m:]
+    Wc, Hc, _ = C.bcd_epoch(ix, W0, H0, p.lam)
+    scale = np.abs(np.concatenate([W.ravel(), H.ravel()])).max()
+    assert np.abs(Wc - W).max() <= 1e-7 * scale and np.abs(Hc - H).max() <= 1e-7 * scale
+    Wr, Hr = W0[:, ::-1].copy(), H0[:, ::-1].copy()
+    Wr, Hr, _ = C.bcd_epoch(ix, Wr, Hr, p.lam)
+    assert np.abs(Wr[:, ::-1] - W).max() > 1e-4 * scale

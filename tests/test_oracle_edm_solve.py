@@ -110,6 +110,82 @@ def test_lipschitz_bound_dominates_the_operator_norm():
     assert bound <= 4.0 * exact
 
 
+def test_lipschitz_bound_is_exact_for_disjoint_pairs():
+    """Pairs without a common point have orthogonal E_p (<E_p, E_q> = ((e_i - e_j)^T
+    (e_k - e_l))^2 = 0), so the Gram of sqrt(w_p) vec(E_p) is diagonal with
+    entries ||E_p||_F^2 w_p = 4 w_p: ||A* A|| = 4 max w, which the bound must equal."""
+    n = 12
+    i = np.arange(0, n, 2)
+    j = np.arange(1, n, 2)
+    w = np.random.default_rng(5).uniform(0.5, 2.0, i.shape[0])
+    assert E.lipschitz(n, i, j, w) == pytest.approx(4.0 * w.max(), rel=1e-14)
+
+
+def test_shift_makes_the_operator_positive_semidefinite():
+    """sigma bounds the negative part of Z = V V^T - alpha L_{w r} - alpha lam J,
+    so Z + sigma I is positive semidefinite (dense eigenvalues).  The case is
+    one stretched pair: x = (e_0 - e_1)/sqrt(2) gives x^T Z x = D/2 - 2c for
+    D = ||v_0 - v_1||^2 and c = alpha (D - d^2), so with d^2 = D/10 the
+    smallest eigenvalue is below -1.3 D while sigma = 2c = 1.8 D: half of the
+    bound would not do."""
+    n = 6
+    rng = np.random.default_rng(6)
+    V = 0.05 * rng.standard_normal((n, 2))
+    V[0], V[1] = [1.0, 0.0], [-1.0, 0.0]
+    V = E.center(V)
+    Dist = float(np.sum((V[0] - V[1]) ** 2))
+    i, j, d, w = E.pair_arrays([0], [1], [np.sqrt(0.1 * Dist)], 1.0)
+    Zop = E.z_operator(V, i, j, d, w, 0.0, 1.0)
+    Z = Zop.z(np.eye(n))
+    ev = np.linalg.eigvalsh(0.5 * (Z + Z.T))
+    assert ev.min() <= -1.3 * Dist
+    assert ev.min() + Zop.sigma >= -1e-12 * Zop.sigma
+    assert ev.min() + 0.5 * Zop.sigma < 0
+
+
+def test_rank_rule_of_the_qsdp_experiments():
+    """Supplement, QSDP implementation details: if every computed eigenvalue is
+    positive the next step computes k + floor(n / 20) of them (capped at
+    k_max here), otherwise as many as were positive; the new factor keeps the
+    positive pairs, V = U_+ diag(sqrt(mu_+))."""
+    n, k = 100, 5
+    U = np.linalg.qr(np.random.default_rng(7).standard_normal((n, k)))[0]
+    V, rank, k_next = E.prox_from_eig(U, np.array([5.0, 4.0, 3.0, 2.0, 1.0]), k, 40, n)
+    assert (rank, k_next) == (5, 10)
+    assert np.allclose(V, U * np.sqrt([5.0, 4.0, 3.0, 2.0, 1.0]))
+    assert E.prox_from_eig(U, np.array([5.0, 4.0, 3.0, 2.0, 1.0]), k, 8, n)[2] == 8
+    V, rank, k_next = E.prox_from_eig(U, np.array([3.0, 2.0, 0.0, -1.0, -2.0]), k, 40, n)
+    assert (rank, k_next) == (2, 2)
+    assert np.allclose(V, U[:, :2] * np.sqrt([3.0, 2.0]))
+
+
+@pytest.mark.parametrize("n, k0", [(20, 3), (40, 6)])
+def test_initial_rank_is_fifteen_percent_of_n(n, k0):
+    """Supplement, QSDP implementation details: k_0 = min(100, floor(0.15 n))
+    eigenpairs in the initial step."""
+    p, i, j, d, w = _chain(n, 14)
+    lam = O.edm_lambda(n, d)
+    alpha = 1.0 / E.lipschitz(n, i, j, w)
+    _, info = E.init_step(n, i, j, d, w, lam, alpha, 50, O.Options())
+    assert info.mu.shape[0] == k0
+
+
+def test_solve_cycle_is_bm_phase_then_pg_step_with_alpha_one_over_l():
+    """Algorithm 1 on the QSDP (supplement, implementation details): each cycle
+    runs the BM phase from W_t, then one inexact PG step with the fixed step
+    alpha = 1/L from its result."""
+    n = 20
+    p, i, j, d, w = _chain(n, 15)
+    lam = O.edm_lambda(n, d)
+    opt = O.Options()
+    alpha = 1.0 / E.lipschitz(n, i, j, w)
+    st0, _ = E.init_step(n, i, j, d, w, lam, alpha, 10, opt)
+    V, _ = E.bm_phase(st0.V, i, j, d, w, lam, opt.bm_epochs)
+    st1, _ = E.prox_step(E.EdmState(V=V, U=st0.U, k_eig=st0.k_eig, t=st0.t), i, j, d, w, lam, alpha, 10, opt)
+    _, F, _ = E.solve(n, i, j, d, w, lam, 10, opt, max_outer=1, tol=0.0)
+    assert F[1] == E.objective(st1.V, i, j, d, w, lam)
+
+
 def test_pg_step_equals_dense_exact_projection():
     p, i, j, d, w = _chain(40, 13)
     n = p.n

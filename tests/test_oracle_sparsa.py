@@ -2,9 +2,12 @@
 evaluations and closed forms: Eq. "trace" and the nuclear norm against the
 dense matrices, <dX, dG> against the dense gradient difference, alpha_BB = 1
 with full observation, Eq. "back" / Eq. "decrease" re-evaluated densely for
-every accepted step, no backtracking when alpha_max <= 1/L, and the SpaRSA
+every step (with the flag naming the test that held, and the trial one
+reduction earlier failing both), Eq. "proxBB" from the two points where the
+PG steps were taken, no backtracking when alpha_max <= 1/L, and the SpaRSA
 solve reaching the dense soft-impute optimum."""
 import numpy as np
+import pytest
 
 from oracle import bm_oracle as O
 from oracle import sparsa_oracle as S
@@ -69,25 +72,64 @@ def test_full_observation_bb_step_is_one_over_lipschitz():
     assert abs(a - 1.0) <= 1e-12
 
 
-def test_accepted_steps_satisfy_back_or_decrease_densely():
+@pytest.mark.parametrize("delta", [0.995, 0.5])
+def test_accepted_steps_satisfy_back_or_decrease_densely(delta):
+    """Every accepted step against Eq. "back" / Eq. "decrease" evaluated with
+    dense matrices.  With delta = 0.5 the tests part ways (steps accepted by
+    Eq. "decrease" alone occur), with the default 0.995 they nearly agree."""
     p, ix = _small(seed=13)
     opt = O.Options(lmsvd_tol=1e-12, lmsvd_imax=200)
-    o = S.BbOptions()
+    o = S.BbOptions(delta=delta)
     st, _ = O.init_step(ix, p.lam, 4, 20, opt)
     prev = None
     seen_bb = False
+    backtracked = by_decrease = 0
     for t in range(6):
         st, _ = O.bm_phase(ix, st, p.lam, 3)
         st1, info, bb, prev = S.prox_step_bb(ix, st, p.lam, 20, opt, o, prev)
         assert bb.accepted_by in (1, 2)
         back, dec = S.dense_check(ix, st, st1, p.lam, bb.alpha, o.delta)
         assert back or dec
-        if bb.accepted_by == 1:
-            assert back
+        # the flag names the test that held: 1 for Eq. "back", 2 for Eq.
+        # "decrease" alone
+        assert (bb.accepted_by == 1) == back, (t, bb, back, dec)
+        if bb.accepted_by == 2:
+            assert dec
         assert abs(bb.alpha - bb.alpha_bb * o.beta ** bb.backtracks) <= 1e-15 * bb.alpha_bb
+        # the smallest i: the trial one reduction earlier satisfies neither test
+        if bb.backtracks:
+            a_prev = bb.alpha / o.beta
+            st_prev, _ = O.prox_step(ix, st, p.lam, 20, opt, alpha=a_prev)
+            assert not any(S.dense_check(ix, st, st_prev, p.lam, a_prev, o.delta)), (t, bb)
+            backtracked += 1
+        by_decrease += bb.accepted_by == 2
         seen_bb = seen_bb or (t > 0 and bb.alpha_bb > 1.99)
         st = st1
     assert seen_bb   # the BB value exceeds the fixed step on this sampled problem
+    assert backtracked and (by_decrease or delta > 0.9), (backtracked, by_decrease)
+
+
+def test_bb_step_uses_the_points_where_the_pg_steps_were_taken():
+    """Eq. "proxBB" from X_t and X_{t-1}, the last two points where a PG step
+    was taken (after their BM phases), as the step ||dX||^2 / <dX, dG> with
+    dense gradients P_Omega(X - A), clipped to [alpha_min, alpha_max]; the
+    first PG step starts from the fixed step alpha, clipped alike."""
+    p, ix = _small(seed=13)
+    opt = O.Options(lmsvd_tol=1e-12, lmsvd_imax=200)
+    o = S.BbOptions()
+    M, mask = _dense(ix)
+    st, _ = O.init_step(ix, p.lam, 4, 20, opt)
+    st, _ = O.bm_phase(ix, st, p.lam, 3)
+    X0 = st.W @ st.H.T
+    st1, _, bb0, prev = S.prox_step_bb(ix, st, p.lam, 20, opt, o, None)
+    assert bb0.alpha_bb == min(o.alpha_max, max(o.alpha_min, opt.alpha))
+    st1, _ = O.bm_phase(ix, st1, p.lam, 3)
+    X1 = st1.W @ st1.H.T
+    _, _, bb1, _ = S.prox_step_bb(ix, st1, p.lam, 20, opt, o, prev)
+    dX = X1 - X0
+    dG = np.where(mask, X1 - M, 0.0) - np.where(mask, X0 - M, 0.0)
+    expect = min(o.alpha_max, max(o.alpha_min, float(np.sum(dX * dX)) / float(np.sum(dX * dG))))
+    assert bb1.alpha_bb == pytest.approx(expect, rel=1e-9)
 
 
 def test_no_backtracking_when_alpha_at_most_one_over_L():
