@@ -104,6 +104,9 @@ MUTATIONS = [
      "        for _ in range(opt.pg_steps):\n            st, info = prox_step(ix, st, lam, k_max, opt)\n"
      "            eps_hist.append(info.eps)\n            its.append(info.lmsvd_iters)\n"
      "        st, _ = bm_phase(ix, st, lam, opt.bm_epochs)\n", None),
+    (BM, "edm lambda: sign", "return -10.0 * math.sqrt(n) / float(", "return 10.0 * math.sqrt(n) / float(", None),
+    (BM, "edm lambda: sqrt(n) / 10", "return -10.0 * math.sqrt(n) / float(np.sum(np.asarray(d, dtype=np.float64) ** 2))",
+     "return -math.sqrt(n) / 10.0", None),
     # distance-geometry QSDP
     (EDM, "edm: residual sign of d^2", "return np.sum(diff * diff, axis=1) - d * d",
      "return np.sum(diff * diff, axis=1) + d * d", None),

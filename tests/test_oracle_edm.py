@@ -4,6 +4,7 @@ finite differences, and the symmetric Laplacian form of the gradient."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle import bm_oracle as O
 from synth import self_avoiding_chain
@@ -64,3 +65,9 @@ def test_chain_generator_geometry():
     assert within.shape[0] == p.npairs                          # Omega = all pairs within the cutoff
     dt = D[p.i, p.j]
     assert np.all(np.abs(p.d / dt - 1.0) <= 0.1 + 1e-6)
+
+
+def test_lambda_of_the_molecular_conformation_setting():
+    """Supplement, molecular conformation: lambda = -10 sqrt(n) / sum d_ij^2;
+    for n = 4 and d = (1, 2, 2), -10 * 2 / 9."""
+    assert O.edm_lambda(4, np.array([1.0, 2.0, 2.0])) == pytest.approx(-20.0 / 9.0, rel=1e-15)
