@@ -188,11 +188,19 @@ def test_bm_phase_matches_oracle_and_is_monotone(B):
         Fo1 = O.objective(ix, st2.W, st2.H, p.lam)
         assert abs(Fs[1] - Fo1) <= RTOL * Fo1
         assert all(b <= a * (1 + 1e-6) for a, b in zip(Fs, Fs[1:]))
-        # three CG epochs in one call agree with the oracle's three epochs
+        # three CG epochs in one call agree with the oracle's three epochs, in
+        # the objective and in the product W H^T (measured on GB300 over four
+        # shapes and ranks 8 ... 33: F within 4.3e-8 and W H^T within 3.7e-7
+        # relative after three epochs, 4.4e-7 and 4.1e-7 after six)
         B.bm_set_factors(h, k, W, H)
         F3 = B.bm_bm_phase(h, 3)
         st3, _ = O.bm_phase(ix, st, p.lam, 3)
         Fo3 = O.objective(ix, st3.W, st3.H, p.lam)
-        assert abs(F3 - Fo3) <= 1e-4 * Fo3
+        assert abs(F3 - Fo3) <= RTOL * Fo3
+        Wg, Hg = B.bm_get_factors(h, p.m, p.n)
+        Wo, Ho = (st3.H, st3.W) if ix.transposed else (st3.W, st3.H)
+        Xo = Wo @ Ho.T
+        Xg = Wg.astype(np.float64) @ Hg.astype(np.float64).T
+        assert np.linalg.norm(Xg - Xo) <= RTOL * np.linalg.norm(Xo)
     finally:
         B.bm_destroy(h)
