@@ -43,7 +43,6 @@ alpha_max <= 1/L, and the soft-impute optimum reached by the SpaRSA solve).
 from __future__ import annotations
 
 import dataclasses
-import math
 from typing import Optional
 
 import numpy as np

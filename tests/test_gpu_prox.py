@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import bm_oracle as O
-from synth import named_config, planted_uniform, random_factors
+from synth import named_config, random_factors
 
 pytestmark = pytest.mark.gpu
 
