@@ -20,9 +20,10 @@ Algorithm 1 here:
     "PiX" and Eq. "proxsym", X+ = P_S+(J (X~ - alpha grad f(X~) - alpha lam I) J)
     = P_S+(Z), Z = V V^T - alpha L_{w r} - alpha lam J, J = I - e e^T / n.  The
     leading eigenpairs of Z come from the LmSVD iteration (Algorithm 2) on the
-    shifted operator Z + sigma I (positive semidefinite on ker(e^T), so its
-    leading eigenvectors are those of the largest eigenvalues of Z); X+ keeps
-    the positive part, V+ = U diag(sqrt(mu_+)).
+    shifted operator Z + sigma J (positive semidefinite, equal to Z + sigma I
+    on ker(e^T) and 0 along e, so its leading eigenvectors are those of the
+    largest eigenvalues of Z on ker(e^T)); X+ keeps the positive part,
+    V+ = U diag(sqrt(mu_+)).
 
 Readings (each also in the design notes):
   * alpha = 1/L with L the Gershgorin bound of ||A* A||: the Gram of the
@@ -170,7 +171,11 @@ class ZOperator:
                 - self.alpha * self.lam * center(U))
 
     def zs(self, U):
-        return self.z(U) + self.sigma * U
+        """(Z + sigma J) U: sigma I on ker(e^T), where X+ lives (Lemma "PiX"),
+        and 0 along e, so that rounding along e is not amplified (with
+        sigma I, e would carry the eigenvalue sigma, above every other one
+        once lam > 0 pushes the spectrum on ker(e^T) below zero)."""
+        return self.z(U) + self.sigma * center(U)
 
 
 def z_operator(V, i, j, d, w, lam, alpha):
@@ -201,7 +206,7 @@ class EdmProxInfo:
 
 
 def top_eigpairs(Zop: ZOperator, U0, k, opt: O.Options):
-    """Leading k eigenpairs of Z from LmSVD (Algorithm 2) on Z + sigma I."""
+    """Leading k eigenpairs of Z from LmSVD (Algorithm 2) on Z + sigma J."""
     Uh, theta, iters, _ = O.lmsvd(Zop.zs, U0, p=opt.lmsvd_p, tol=opt.lmsvd_tol, imax=opt.lmsvd_imax,
                                   tau=opt.tau, min_iter=opt.lmsvd_min_iter)
     kk = min(k, Uh.shape[1])

@@ -35,6 +35,14 @@ MUTATIONS = [
     (BM, "loss: F with lam", "F = f + 0.5 * lam * (", "F = f + 1.0 * lam * (", None),
     (BM, "loss: gH without lam", "gH = R.T @ W + lam * H", "gH = R.T @ W", None),
     (BM, "residual: sign", "H[ix.col]) - ix.val", "H[ix.col]) + ix.val", None),
+    (BM, "index: duplicates accepted", "        if np.any(same):\n            raise ValueError", "        if False:\n            raise ValueError", None),
+    (BM, "index: CSC in CSR order", "csc2csr = np.lexsort((r_s, c_s))", "csc2csr = np.lexsort((c_s, r_s))", None),
+    (BM, "codes: non-integers accepted", "if not np.all(v == np.rint(v)) or", "if not np.all(v == v) or", None),
+    (BM, "generator: sine", "* np.cos(2.0 * math.pi * u[1::2])", "* np.sin(2.0 * math.pi * u[1::2])", None),
+    (BM, "generator: 52-bit uniforms", "u = ((z >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)",
+     "u = ((z >> np.uint64(12)).astype(np.float64) + 1.0) * (2.0 ** -52)", None),
+    (BM, "generator: key without the stream", "key = _mix64(np.array([(seed * _GAMMA + stream) & _M64]",
+     "key = _mix64(np.array([(seed * _GAMMA) & _M64]", None),
     # orth (Eq. PUi, orth-W)
     (BM, "orth: one pass", "for pass_no in range(2):", "for pass_no in range(1):", None),
     (BM, "orth: L-image not projected", "                LMh = LMh - LF @ C\n", "                pass\n", None),
@@ -76,6 +84,16 @@ MUTATIONS = [
     (BM, "warm start: U_{t-1} after a BM phase",
      "second = st.W if (st.bm_changed or st.U_prev2 is None) else st.U_prev2",
      "second = st.U_prev2 if st.U_prev2 is not None else st.W", None),
+    (BM, "warm start: xi not projected off U^", "        g = g - Uh0 @ (Uh0.T @ g)\n", "", None),
+    (BM, "warm start: psi scales u_t", "col = ut + st.psi * g if st.u is not None else g",
+     "col = st.psi * ut + g if st.u is not None else g", None),
+    (BM, "warm start: cap k_max", "    cap = k_max + 1\n", "    cap = k_max\n", None),
+    (BM, "init: sketch from the safeguard stream", "G = counter_normal(opt.seed, STREAM_INIT_SKETCH, m * k_init)",
+     "G = counter_normal(opt.seed, STREAM_SAFEGUARD, m * k_init)", None),
+    (BM, "init: sketch drawn column by column", ".reshape(k_init, m).T\n    Q, _ = orth(Zop.L(G)",
+     ".reshape(m, k_init)\n    Q, _ = orth(Zop.L(G)", None),
+    (BM, "solve: stop on the absolute change", "if abs(F_hist[-2] - F) / (1.0 + abs(F_hist[-2])) < tol:",
+     "if abs(F_hist[-2] - F) < tol:", None),
     (BM, "warm start: and-trigger",
      "trig = (st.rank_hist[-1] == st.rank_hist[-2]) or (st.prev_warm_cols <= st.rank_hist[-1] + 1)",
      "trig = (st.rank_hist[-1] == st.rank_hist[-2]) and (st.prev_warm_cols <= st.rank_hist[-1] + 1)", None),
@@ -121,11 +139,14 @@ MUTATIONS = [
     (EDM, "edm: Z without alpha", "c = alpha * w * r", "c = w * r", None),
     (EDM, "edm: Z shift sign of lam J", "- self.alpha * self.lam * center(U))", "+ self.alpha * self.lam * center(U))", None),
     (EDM, "edm: shift not removed", "return Uh[:, :kk], theta[:kk] - Zop.sigma, iters", "return Uh[:, :kk], theta[:kk], iters", None),
+    (EDM, "edm: shift by sigma I", "return self.z(U) + self.sigma * center(U)", "return self.z(U) + self.sigma * U", None),
     (EDM, "edm: shift half the bound", "sigma = 2.0 * float(np.max(rowabs))", "sigma = 1.0 * float(np.max(rowabs))", None),
     (EDM, "edm: factor mu not sqrt(mu)", "Vn = U[:, pos] * np.sqrt(mu[pos])", "Vn = U[:, pos] * mu[pos]", None),
     (EDM, "edm: rank rule growth n / 10", "k_next = min(k_max, k_eig + n // 20)", "k_next = min(k_max, k_eig + n // 10)", None),
     (EDM, "edm: rank rule keeps k when truncated", "k_next = max(1, rank)", "k_next = max(1, k_eig)", None),
-    (EDM, "edm: warm start not centred", "Q, _ = O.orth(center(M), max_cols=k)", "Q, _ = O.orth(M, max_cols=k)", None),
+    (EDM, "edm: warm start not centred", "Q, _ = O.orth(center(M), max_cols=k)", "Q, _ = O.orth(M, max_cols=k)",
+     "U_t and V already lie in ker(e^T), so the centring only removes rounding, and with the shift sigma J a "
+     "component along e decays (eigenvalue 0) and is never among the leading pairs"),
     (EDM, "edm: initial rank 0.1 n", "k0 = max(1, min(100, int(0.15 * n), k_max))", "k0 = max(1, min(100, int(0.1 * n), k_max))", None),
     (EDM, "edm: step 1.99 / L", "alpha = 1.0 / lipschitz(n, i, j, w)\n    st, _ = init_step",
      "alpha = 1.99 / lipschitz(n, i, j, w)\n    st, _ = init_step", None),
@@ -135,6 +156,12 @@ MUTATIONS = [
      "        st, info = prox_step(st, i, j, d, w, lam, alpha, k_max, opt)\n"
      "        V, _ = bm_phase(st.V, i, j, d, w, lam, opt.bm_epochs)\n        st = EdmState(V=V, U=st.U, k_eig=st.k_eig, t=st.t)\n",
      None),
+    (EDM, "edm: fill columns from stream t", "G = O.counter_normal(seed, STREAM_EDM_FILL + t, n * extra)",
+     "G = O.counter_normal(seed, t, n * extra)", None),
+    (EDM, "edm: initial start not centred", "U, mu, iters = top_eigpairs(Zop, center(G), k0, opt)",
+     "U, mu, iters = top_eigpairs(Zop, G, k0, opt)",
+     "with the shift sigma J, e carries the eigenvalue 0, the bottom of the positive semidefinite shifted "
+     "spectrum: a start component along e decays and is never among the leading pairs"),
     # SpaRSA step rule
     (BB, "bb: trace cross factor", "return t11 + t00 - 2.0 * t01", "return t11 + t00 - t01", None),
     (BB, "bb: nuclear norm without sqrt", "return float(np.sum(np.sqrt(np.maximum(ev, 0.0))))",
@@ -149,11 +176,14 @@ MUTATIONS = [
     (BB, "bb: previous point after the step", "return st1, info, bb, BbPoint(st.W.copy(), st.H.copy(), r)",
      "return st1, info, bb, BbPoint(st1.W.copy(), st1.H.copy(), O.residual(ix, st1.W, st1.H))", None),
     (BB, "bb: first step alpha 1", "a0 = bb_alpha(st.W, st.H, r, prev, o, opt.alpha)", "a0 = bb_alpha(st.W, st.H, r, prev, o, 1.0)", None),
+    (BB, "bb: solve forgets the previous point", "st, info, bb, prev = prox_step_bb(ix, st, lam, k_max, opt, o, prev)",
+     "st, info, bb, _ = prox_step_bb(ix, st, lam, k_max, opt, o, prev)", None),
     # column-block coordinate descent
     (BCD, "bcd: block gradient without lam", "gw = R @ h + lam * w", "gw = R @ h", None),
     (BCD, "bcd: b without the H term", "b = dw[ri] * h[cj] + w[ri] * dh[cj]", "b = dw[ri] * h[cj]", None),
     (BCD, "bcd: quartic without lam in s^2", "+ 0.5 * lam * (float(dw @ dw) + float(dh @ dh)),", ",", None),
     (BCD, "bcd: residual update without s^2", "r = r + s * b + s * s * cc", "r = r + s * b", None),
+    (BCD, "bcd: phase reports the first block", "F.append(tr[-1] if tr else", "F.append(tr[0] if tr else", None),
     (BCD, "bcd: blocks in reverse order", "for c in range(W.shape[1]):", "for c in reversed(range(W.shape[1])):", None),
 ]
 
@@ -201,6 +231,9 @@ def main():
     a = ap.parse_args()
     work = a.workdir or tempfile.mkdtemp(prefix="oracle_mutations_")
     idx = a.which or list(range(len(MUTATIONS)))
+    bad_idx = [i for i in idx if not 0 <= i < len(MUTATIONS)]
+    if bad_idx:
+        ap.error(f"no mutation {bad_idx}: indices run from 0 to {len(MUTATIONS) - 1}")
     with cf.ThreadPoolExecutor(a.jobs) as ex:
         res = dict(zip(idx, ex.map(lambda i: run_one(i, work), idx)))
     bad = 0

@@ -114,3 +114,14 @@ def test_sweep_is_exact_block_steps_in_column_order():
     Wr, Hr = W0[:, ::-1].copy(), H0[:, ::-1].copy()
     Wr, Hr, _ = C.bcd_epoch(ix, Wr, Hr, p.lam)
     assert np.abs(Wr[:, ::-1] - W).max() > 1e-4 * scale
+
+
+def test_phase_reports_the_objective_after_each_sweep():
+    p, ix = _small(seed=7)
+    rng = np.random.default_rng(3)
+    W0, H0 = rng.standard_normal((ix.m, 4)) * 0.5, rng.standard_normal((ix.n, 4)) * 0.5
+    W, H, F = C.bcd_phase(ix, W0, H0, p.lam, 2)
+    W1, H1, _ = C.bcd_phase(ix, W0, H0, p.lam, 1)
+    assert len(F) == 2
+    assert abs(F[0] - O.objective(ix, W1, H1, p.lam)) <= 1e-12 * F[0]
+    assert abs(F[1] - O.objective(ix, W, H, p.lam)) <= 1e-12 * F[1]

@@ -216,3 +216,32 @@ def test_solve_reaches_the_dense_convex_optimum():
     ev = np.linalg.eigvalsh(X_star)
     assert ranks[-1] == int(np.sum(ev > 1e-6 * ev.max()))
     assert np.abs(st.V.sum(axis=0)).max() <= 1e-8
+
+
+def test_warm_start_fills_from_the_counter_stream_of_the_step():
+    """With no previous vectors the warm start of step t is the centred
+    Gaussian block of counter stream 2000 + t, orthonormalised."""
+    n, k, t = 15, 4, 3
+    st = E.EdmState(V=np.zeros((n, 0)), U=np.zeros((n, 0)), k_eig=k, t=t)
+    Q = E.warm_start(st, n, k, 0, t)
+    G = O.counter_normal(0, 2000 + t, n * k).reshape(k, n).T
+    G = G - G.mean(axis=0)
+    P = Q @ Q.T
+    assert Q.shape == (n, k)
+    assert np.abs(Q.T @ Q - np.eye(k)).max() <= 1e-12
+    assert np.linalg.norm(G - P @ G) <= 1e-10 * np.linalg.norm(G)
+
+
+def test_initial_eigenvectors_stay_orthogonal_to_e():
+    """Lemma "PiX": X+ = P_S+(J Z J) lives on ker(e^T), and the initial step
+    starts from centred Gaussians, so every computed eigenvector is orthogonal
+    to e, also when some of the k_0 leading eigenvalues are not positive
+    (lambda > 0, the kernel-estimation sign, where e's eigenvalue 0 of Z would
+    otherwise compete)."""
+    n = 40
+    p, i, j, d, w = _chain(n, 16)
+    alpha = 1.0 / E.lipschitz(n, i, j, w)
+    lam = 50.0 * float(np.max(d * d))
+    st, info = E.init_step(n, i, j, d, w, lam, alpha, 20, O.Options(lmsvd_tol=1e-12, lmsvd_imax=300))
+    assert np.min(info.mu) <= 0.0
+    assert np.abs(st.U.T @ np.ones(n)).max() <= 1e-9

@@ -352,3 +352,39 @@ def test_counter_generator_matches_published_splitmix64():
     cdf = 0.5 * (1 + np.vectorize(math.erf)(xs / math.sqrt(2)))
     ks = np.max(np.abs(cdf - np.arange(1, xs.size + 1) / xs.size))
     assert ks < 0.01
+
+
+def test_counter_generator_matches_its_definition_in_integer_arithmetic():
+    """counter_normal against its definition evaluated with Python integers
+    and math (no numpy uint64 arithmetic): key = mix64(seed * gamma + stream
+    mod 2^64), u_i = ((mix64(key + i * gamma mod 2^64) >> 11) + 1) / 2^53, and
+    Box and Muller's x_j = sqrt(-2 ln u_2j) cos(2 pi u_2j+1); mix64 is the
+    SplitMix64 finaliser whose published outputs the test above checks."""
+    M = (1 << 64) - 1
+    G = 0x9E3779B97F4A7C15
+
+    def mix(z):
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9 & M
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EB & M
+        return z ^ (z >> 31)
+
+    for seed, stream in ((0, 1), (3, 1000), (12345, 2007)):
+        x = O.counter_normal(seed, stream, 6)
+        key = mix((seed * G + stream) & M)
+        u = [((mix((key + i * G) & M) >> 11) + 1) * 2.0 ** -53 for i in range(12)]
+        ref = [math.sqrt(-2.0 * math.log(u[2 * j])) * math.cos(2.0 * math.pi * u[2 * j + 1]) for j in range(6)]
+        assert np.allclose(x, ref, rtol=1e-14, atol=1e-15), (seed, stream)
+
+
+def test_solve_stops_at_the_first_small_relative_change():
+    """Algorithm 1's outer loop stops at the first cycle whose objective
+    changes by less than tol relative to 1 + |F_prev| (F is in the hundreds
+    here, so an absolute test would stop elsewhere)."""
+    p, ix = _small_problem(m=40, n=60, frac=0.35, rank=3, seed=21, lam=1.0)
+    tol = 1e-4
+    _, info = O.solve(ix, p.lam, 4, 12, O.Options(), max_outer=200, tol=tol)
+    F = info.F_hist
+    rel = [abs(a - b) / (1.0 + abs(a)) for a, b in zip(F, F[1:])]
+    assert F[-1] > 10.0 and len(rel) < 200
+    assert rel[-1] < tol and all(r >= tol for r in rel[:-1])
+    assert any(abs(a - b) >= tol for a, b in zip(F, F[1:]))

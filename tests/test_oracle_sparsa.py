@@ -162,3 +162,21 @@ def test_sparsa_solve_reaches_the_dense_soft_impute_optimum():
     st, F, bbs = S.solve_bb(ix, p.lam, 4, 30, O.Options(), S.BbOptions(), max_outer=400, tol=1e-15)
     assert abs(F[-1] - F_star) <= 1e-8 * F_star
     assert st.W.shape[1] == int(np.sum(sX > 1e-8))
+
+
+def test_sparsa_solve_carries_the_previous_point():
+    """The SpaRSA solve's second PG step takes alpha_BB from the points of the
+    first and second PG steps, as the step-by-step sequence does."""
+    p, ix = _small(seed=13)
+    opt = O.Options(lmsvd_tol=1e-12, lmsvd_imax=200)
+    o = S.BbOptions()
+    _, _, bb_hist = S.solve_bb(ix, p.lam, 4, 20, opt, o, max_outer=2, tol=0.0)
+    st, _ = O.init_step(ix, p.lam, 4, 20, opt)
+    prev = None
+    seq = []
+    for _ in range(2):
+        st, _ = O.bm_phase(ix, st, p.lam, opt.bm_epochs)
+        st, _, bb, prev = S.prox_step_bb(ix, st, p.lam, 20, opt, o, prev)
+        seq.append(bb.alpha_bb)
+    assert [b.alpha_bb for b in bb_hist] == seq
+    assert seq[1] != seq[0]
