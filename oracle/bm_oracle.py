@@ -430,10 +430,12 @@ def warm_start(st: State, k_max: int, opt: Options):
         nut2 = float(ut @ ut)
         if nut2 > 0:
             g = g - ut * (float(ut @ g) / nut2)
-        g = g / np.linalg.norm(g)
-        col = ut + st.psi * g if st.u is not None else g
-        extra, _ = orth(col[:, None], F=Uh0 if Uh0.shape[1] else None, tau=opt.tau)
-        Uh0 = np.hstack([Uh0, extra])
+        ng = float(np.linalg.norm(g))
+        if ng > 0:   # else [U^, u_t] spans R^m: no xi_t orthogonal to it, no column
+            g = g / ng
+            col = ut + st.psi * g if st.u is not None else g
+            extra, _ = orth(col[:, None], F=Uh0 if Uh0.shape[1] else None, tau=opt.tau)
+            Uh0 = np.hstack([Uh0, extra])
     return Uh0
 
 

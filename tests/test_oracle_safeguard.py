@@ -157,3 +157,15 @@ def test_warm_start_is_capped_at_k_max_plus_one():
     assert Uh0.shape[1] == 5 and np.allclose(Uh0, U[:, :5])
     Uh0 = O.warm_start(_state(U[:, :3], W, [6, 6], 3, u=np.ones(m)), k_max=4, opt=_opt())
     assert Uh0.shape[1] == 5          # base 3 + 2 from W; full, so no safeguard column
+
+
+def test_no_column_when_the_basis_and_u_span_the_whole_space():
+    """m = 2, U^ = e_1 and u_t = e_2: no xi_t is orthogonal to [U^, u_t], so
+    the safeguard adds no column (and forms no 0/0 on the way)."""
+    import warnings
+    U = np.array([[1.0], [0.0]])
+    W = U * 2.0
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        Uh0 = O.warm_start(_state(U, W, [1, 1], 9, u=np.array([0.0, 3.0])), k_max=3, opt=_opt())
+    assert Uh0.shape == (2, 1) and np.allclose(np.abs(Uh0[:, 0]), [1.0, 0.0])
