@@ -388,3 +388,25 @@ def test_solve_stops_at_the_first_small_relative_change():
     assert F[-1] > 10.0 and len(rel) < 200
     assert rel[-1] < tol and all(r >= tol for r in rel[:-1])
     assert any(abs(a - b) >= tol for a, b in zip(F, F[1:]))
+
+
+def test_solve_degenerate_cases():
+    """Closed forms of (MC) at its degenerate inputs, with no 0/0 on the way:
+    empty Omega gives X = 0 and F = 0; a single observed entry a gives the
+    scalar soft-threshold x = sign(a) max(|a| - lam, 0), F = (x - a)^2 / 2 +
+    lam |x|; full observation with lam above the largest singular value
+    gives X = 0 and F = ||A||^2 / 2."""
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        st, info = O.solve(O.build_index(5, 7, [], [], []), 0.5, 3, 4, O.Options(), max_outer=5)
+        assert st.W.shape[1] == 0 and info.F_hist[-1] == 0.0
+        for a, lam in ((3.0, 0.5), (-2.0, 0.7), (0.4, 1.0)):
+            st, info = O.solve(O.build_index(1, 1, [0], [0], [a]), lam, 1, 1, O.Options(), max_outer=50, tol=1e-15)
+            x = math.copysign(max(abs(a) - lam, 0.0), a)
+            X = (st.W @ st.H.T)[0, 0] if st.W.shape[1] else 0.0
+            assert abs(X - x) <= 1e-12 and abs(info.F_hist[-1] - (0.5 * (x - a) ** 2 + lam * abs(x))) <= 1e-12
+        A, ix = _full_problem(6, 9, seed=8)
+        lam = 1.01 * np.linalg.svd(A, compute_uv=False)[0]
+        st, info = O.solve(ix, lam, 3, 5, O.Options(), max_outer=20)
+        assert st.W.shape[1] == 0 and abs(info.F_hist[-1] - 0.5 * np.sum(A * A)) <= 1e-12 * np.sum(A * A)
