@@ -245,3 +245,20 @@ def test_initial_eigenvectors_stay_orthogonal_to_e():
     st, info = E.init_step(n, i, j, d, w, lam, alpha, 20, O.Options(lmsvd_tol=1e-12, lmsvd_imax=300))
     assert np.min(info.mu) <= 0.0
     assert np.abs(st.U.T @ np.ones(n)).max() <= 1e-9
+
+
+def test_large_lambda_gives_the_zero_solution():
+    """For lam above the largest eigenvalue of sum w d^2 E_ij the initial Z_{-1}
+    = alpha (L_{w d^2} - lam J) is negative semidefinite on ker(e^T), so X_0 = 0,
+    and X = 0 is optimal (f's gradient at 0 is -L_{w d^2}, and lam <I, .> beats
+    it on the feasible set): rank 0 and F = 1/2 sum w d^4 throughout."""
+    import warnings
+    n = 12
+    p, i, j, d, w = _chain(n, 18)
+    Ld = E.laplacian_apply(n, i, j, w * d * d, np.eye(n))
+    lam = 1.5 * float(np.linalg.eigvalsh(Ld).max())
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        st, F, ranks = E.solve(n, i, j, d, w, lam, 6, O.Options(), max_outer=5)
+    assert st.V.shape[1] == 0 and all(r == 0 for r in ranks)
+    assert F[-1] == pytest.approx(0.5 * float(np.sum(w * d ** 4)), rel=1e-14)
