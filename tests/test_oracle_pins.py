@@ -410,3 +410,20 @@ def test_solve_degenerate_cases():
         lam = 1.01 * np.linalg.svd(A, compute_uv=False)[0]
         st, info = O.solve(ix, lam, 3, 5, O.Options(), max_outer=20)
         assert st.W.shape[1] == 0 and abs(info.F_hist[-1] - 0.5 * np.sum(A * A)) <= 1e-12 * np.sum(A * A)
+
+
+def test_stored_tiny_optimum_is_the_oracle_solve():
+    """tests/golden/tiny_optimum.txt (written by make_tiny_optimum.py, the
+    target of the time-to-objective benchmark) is what the oracle's
+    Algorithm 1 gives now, bit for bit: objective, rank and cycle count."""
+    vals = {}
+    for line in open(os.path.join(GOLDEN, "tiny_optimum.txt")):
+        if not line.startswith("#"):
+            key, v = line.split()
+            vals[key] = v
+    from synth import named_config
+    p = named_config("tiny")
+    ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
+    st, info = O.solve(ix, p.lam, 8, 64, O.Options(), max_outer=400, tol=1e-14)
+    assert repr(info.F_hist[-1]) == vals["F_star"]
+    assert st.W.shape[1] == int(vals["rank"]) and info.outer == int(vals["cycles"])
