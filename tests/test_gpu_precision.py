@@ -6,9 +6,9 @@ recommendation-scale sizes (480,189 x 17,770 at k = 64 and 1,000,990 x
 624,961 at k = 127): loss 6e-9 and 3e-8 relative, gradient rows at most
 2.3e-3 relative (median 1.6e-3, the bfloat16 rounding 2^-9 of the gathered
 rows).  On this test's smaller problem (160,000 entries, errors average
-over fewer terms) a bfloat16 emulation of the gathers gives at most: loss
-2.8e-6, gradient 1.6e-3 (Frobenius), per-row ratio 2.1e-3 with the
-rounding-scale floor of tests/parity.py.  The bounds below are twice those
+over fewer terms) a bfloat16 model of the gathers (tests/test_bf16_gather_model.py)
+gives at most: loss 2.8e-6, gradient 1.6e-3 (Frobenius), per-row ratio 2.1e-3
+with the rounding-scale floor of tests/parity.py.  The bounds below are twice those
 figures.  A solve in this mode refines its
 final iterations in FP32 and must reach the plain FP32 solve's objective
 within 1e-4 relative.
