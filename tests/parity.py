@@ -16,8 +16,9 @@ Why a_i: when a row's exact gradient nearly cancels (a scalar gradient at
 rank 1 that sums to almost zero), no FP32 evaluation order resolves it to
 1e-5 of its own norm; a plain sequential FP32 sum of the same terms reaches
 4e-5 and 3e-4 of the fixed floor alone on the rank-1 test cases.  A dropped
-or doubled entry still errs by a whole term |r_ij| ||x_j||, about sqrt(N_i)
-times a_i, far above 1e-5 a_i.
+or doubled entry still errs by a whole term |r_ij| ||x_j||, about
+a_i / sqrt(N_i), far above 1e-5 a_i for any N_i below 1e10
+(tests/test_fp32_rounding_model.py plants both).
 """
 import numpy as np
 

@@ -62,3 +62,34 @@ def test_fp32_order_meets_the_per_row_criterion(shape, k):
     if k == 1:
         bare = max(row_error_ratio(gW, gWo).max(), row_error_ratio(gH, gHo).max())
         assert bare > 1e-5, bare
+
+
+@pytest.mark.parametrize("k", [1, 64])
+def test_criterion_catches_a_dropped_or_doubled_entry(k):
+    """One entry dropped from (or counted twice in) a row changes the row by
+    a whole term |r_e| ||x_j||, about a_i / sqrt(N_i) for a row of N_i terms:
+    far above 1e-5 a_i for any N_i below 1e10, so the criterion flags it, on
+    the FP32 model's rows, long and short."""
+    p = named_config("small", m=20_000, n=2_500, nnz=400_000, seed=7, k_max=127)
+    ix = O.build_index(p.m, p.n, p.rows, p.cols, p.vals.astype(np.float64))
+    W, H = random_factors(p.m, p.n, k, seed=k, scale=0.4)
+    Wi, Hi = (H, W) if ix.transposed else (W, H)
+    ri = ix.rows_of_entries()
+    r32 = (np.einsum("ek,ek->e", Wi[ri], Hi[ix.col]).astype(np.float32)
+           - ix.val.astype(np.float32))
+    gW = _fp32_rows(ix.row_ptr, ix.col, Wi, Hi, r32, p.lam)
+    W64, H64 = Wi.astype(np.float64), Hi.astype(np.float64)
+    _, _, gWo, _, r = O.loss_grad(ix, W64, H64, p.lam)
+    aW, _ = grad_rounding_scales(ix, r, W64, H64, p.lam)
+    deg = np.diff(ix.row_ptr)
+    rng = np.random.default_rng(k)
+    picks = [int(np.argmax(deg)), int(np.argmin(deg))] + list(rng.choice(ix.m, 30, replace=False))
+    for i in picks:
+        e = int(ix.row_ptr[i] + rng.integers(deg[i]))
+        term = r32[e] * Hi[ix.col[e]]
+        if not np.any(term):
+            continue
+        for sign in (-1.0, 1.0):                     # dropped, doubled
+            g = gW.copy()
+            g[i] += np.float32(sign) * term
+            assert row_error_ratio(g, gWo, extra=aW)[i] > 1e-5, (i, deg[i], sign)
