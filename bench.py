@@ -470,6 +470,11 @@ def run_reference(args):
     dist, rank, ws = _dist_cpu()
     if rank != 0:
         return None
+    if args.mode not in ("grad", "cycle"):
+        return {"impl": "reference",
+                "unavailable": ("the reference arm (the FP64 oracle on the host cores) is timed for --mode grad "
+                                "and --mode cycle; in tto, edm and edm_solve the oracle's own figure is the "
+                                "line's cpu_baseline, serve and bcd have no oracle timing")}
     from synth import named_config
     p = named_config(args.config)
     from oracle import bm_oracle as O

@@ -60,3 +60,14 @@ def test_peaks_come_from_the_measured_file_else_the_fallback(tmp_path, monkeypat
 def test_replicas_of_one_rank_report_the_rank_itself():
     ms, units, rate = bench.replica_throughput(None, 4.0, 1000)
     assert (ms, units) == (4.0, 1000.0) and rate == 250_000.0
+
+
+def test_reference_arm_names_its_modes():
+    """The reference arm times the oracle for the grad and cycle modes only;
+    any other mode gets the unavailable line instead of another mode's figure."""
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--mode", "edm"],
+                         capture_output=True, text=True, timeout=120, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-500:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "grad" in line["unavailable"]
