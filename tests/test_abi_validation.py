@@ -109,3 +109,29 @@ def test_small_eigensolver_rejects_bad_arguments(n, mode, match):
     st = L.bm_sym_eig(S.ctypes.data, n, None, None, mode, None)
     assert st == INVALID
     assert match in L.bm_dense_last_error().decode()
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: without libbm.so every entry point raises."""
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "LIB_PATH", "/nonexistent/libbm.so")
+    r, c, v = _coo()
+    with pytest.raises(RuntimeError, match="is missing"):
+        B.bm_create(5, 5, r, c, v, 0.5, 2)
+    with pytest.raises(RuntimeError, match="is missing"):
+        B.bm_default_options()
+
+
+def test_package_never_imports_the_oracle():
+    """The library's Python side is marshalling only: importing the package
+    and loading the library pulls in no module of the oracle (checked in a
+    fresh interpreter, as a user would run it)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; import paper_2204_14067_gb300 as P; P.lib(); P.bm_default_options(); "
+            "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
+            "assert not bad, bad; print('clean')")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120, cwd=root)
+    assert out.returncode == 0 and "clean" in out.stdout, out.stderr[-500:]
