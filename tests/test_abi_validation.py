@@ -1,7 +1,9 @@
 """Argument validation of the C ABI, on the CPU: every call here is rejected
 with BM_ERR_INVALID and a message before the library touches CUDA, so the
 checks of include/bm.h's error contracts run without a GPU (the library is
-loaded through the same binding the GPU tests use)."""
+loaded through the same binding the GPU tests use).  Also: without the
+library every entry point raises (there is no fallback), and the package
+imports nothing from the oracle."""
 import ctypes
 import math
 
