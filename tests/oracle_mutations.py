@@ -176,6 +176,8 @@ MUTATIONS = [
     (BB, "bb: previous point after the step", "return st1, info, bb, BbPoint(st.W.copy(), st.H.copy(), r)",
      "return st1, info, bb, BbPoint(st1.W.copy(), st1.H.copy(), O.residual(ix, st1.W, st1.H))", None),
     (BB, "bb: first step alpha 1", "a0 = bb_alpha(st.W, st.H, r, prev, o, opt.alpha)", "a0 = bb_alpha(st.W, st.H, r, prev, o, 1.0)", None),
+    (BB, "bb: exhausted search keeps the first trial", "        out = (st1, info, BbInfo(a0, a, i, 1 if back else (2 if dec else 0)))",
+     "        out = out or (st1, info, BbInfo(a0, a, i, 1 if back else (2 if dec else 0)))", None),
     (BB, "bb: solve forgets the previous point", "st, info, bb, prev = prox_step_bb(ix, st, lam, k_max, opt, o, prev)",
      "st, info, bb, _ = prox_step_bb(ix, st, lam, k_max, opt, o, prev)", None),
     # column-block coordinate descent

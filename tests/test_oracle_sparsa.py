@@ -180,3 +180,23 @@ def test_sparsa_solve_carries_the_previous_point():
         seq.append(bb.alpha_bb)
     assert [b.alpha_bb for b in bb_hist] == seq
     assert seq[1] != seq[0]
+
+
+def test_exhausted_backtracking_keeps_the_last_trial():
+    """A step of 1000 (alpha_min = alpha_max) satisfies neither test, nor do
+    its two reductions by beta = 0.9: the step ends after max_backtracks
+    reductions with flag 0 and keeps the last trial, X_{t+1} at 810 (the
+    reading stated in the oracle's notes), and densely neither test holds."""
+    p, ix = _small(seed=13)
+    opt = O.Options(lmsvd_tol=1e-12, lmsvd_imax=200, alpha=1e3)
+    o = S.BbOptions(alpha_min=1e3, alpha_max=1e3, beta=0.9, max_backtracks=2)
+    st, _ = O.init_step(ix, p.lam, 4, 20, opt)
+    st, _ = O.bm_phase(ix, st, p.lam, 3)
+    st1, _, bb, _ = S.prox_step_bb(ix, st, p.lam, 20, opt, o, None)
+    assert (bb.accepted_by, bb.backtracks) == (0, 2)
+    assert bb.alpha == pytest.approx(810.0, rel=1e-15)
+    last, _ = O.prox_step(ix, st, p.lam, 20, opt, alpha=810.0)
+    assert np.array_equal(st1.W, last.W) and np.array_equal(st1.H, last.H)
+    for a in (1000.0, 900.0, 810.0):
+        trial, _ = O.prox_step(ix, st, p.lam, 20, opt, alpha=a)
+        assert not any(S.dense_check(ix, st, trial, p.lam, a, o.delta))
