@@ -370,6 +370,16 @@ bm_status bm_sym_eig(const double* S, int32_t n, double* evals, double* evecs, i
  * The batch owns a stream; the handles' own streams are synchronised first.
  * A handle must not be used elsewhere while its batch call runs, and must
  * outlive the batch.
+ *
+ * bm_batch_create -- hs: bm_handle[count] (read during the call; the batch
+ *   keeps the handles, not the array), count >= 1; *out receives the batch
+ *   (NULL on failure).  Errors: BM_ERR_INVALID for a NULL array, output or
+ *   handle, handles on different devices or in different precision modes,
+ *   a handle listed twice; BM_ERR_CUDA if its stream cannot be created.
+ * bm_batch_destroy -- waits for the batch's stream, then frees the batch,
+ *   its graph and its stream (not the handles).  NULL is ignored.
+ * bm_batch_last_error -- the message of the batch's last failed call (b =
+ *   NULL: of this thread's last failed bm_batch_create).
  */
 typedef struct bm_batch_ctx* bm_batch;
 bm_status bm_batch_create(bm_handle* hs, int32_t count, bm_batch* out);
