@@ -162,6 +162,10 @@ MUTATIONS = [
      "U, mu, iters = top_eigpairs(Zop, G, k0, opt)",
      "with the shift sigma J, e carries the eigenvalue 0, the bottom of the positive semidefinite shifted "
      "spectrum: a start component along e decays and is never among the leading pairs"),
+    (EDM, "edm dense reference: off-diagonal gradient doubled", "    np.add.at(G, (i, j), -c)\n", "    np.add.at(G, (i, j), -2.0 * c)\n", None),
+    (EDM, "edm dense reference: solve steps with lam / 2",
+     "Xn = dense_project(Y - alpha * (dense_grad_f(Y, i, j, d, w) + lam * np.eye(n)))",
+     "Xn = dense_project(Y - alpha * (dense_grad_f(Y, i, j, d, w) + 0.5 * lam * np.eye(n)))", None),
     # SpaRSA step rule
     (BB, "bb: trace cross factor", "return t11 + t00 - 2.0 * t01", "return t11 + t00 - t01", None),
     (BB, "bb: nuclear norm without sqrt", "return float(np.sum(np.sqrt(np.maximum(ev, 0.0))))",

@@ -262,3 +262,32 @@ def test_large_lambda_gives_the_zero_solution():
         st, F, ranks = E.solve(n, i, j, d, w, lam, 6, O.Options(), max_outer=5)
     assert st.V.shape[1] == 0 and all(r == 0 for r in ranks)
     assert F[-1] == pytest.approx(0.5 * float(np.sum(w * d ** 4)), rel=1e-14)
+
+
+def test_dense_reference_gradient_and_optimality():
+    """The dense references themselves: dense_grad_f against central
+    differences of dense_objective's smooth part (symmetric perturbations
+    E_ab + E_ba), and dense_solve's result is a fixed point of the projected
+    gradient map X = P_X(X - alpha (grad f(X) + lam I)), which for the convex
+    QSDP is its optimality condition (P_X pinned by the variational-inequality
+    test above)."""
+    n = 30
+    p, i, j, d, w = _chain(n, 17)
+    lam = O.edm_lambda(n, d)
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((n, n))
+    X = A @ A.T / n
+    G = E.dense_grad_f(X, i, j, d, w)
+    h = 1e-6
+    for a, b in ((0, 1), (3, 3), (5, 17), (29, 2)):
+        D = np.zeros((n, n))
+        D[a, b] += 1.0
+        D[b, a] += 1.0
+        fp = E.dense_objective(X + h * D, i, j, d, w, 0.0)
+        fm = E.dense_objective(X - h * D, i, j, d, w, 0.0)
+        assert abs((fp - fm) / (2 * h) - float(np.sum(G * D))) <= 1e-6 * (1 + abs(float(np.sum(G * D))))
+    X_star, F_star = E.dense_solve(n, i, j, d, w, lam)
+    alpha = 1.0 / E.lipschitz(n, i, j, w)
+    step = E.dense_project(X_star - alpha * (E.dense_grad_f(X_star, i, j, d, w) + lam * np.eye(n)))
+    assert np.linalg.norm(step - X_star) <= 1e-7 * np.linalg.norm(X_star)
+    assert F_star == pytest.approx(E.dense_objective(X_star, i, j, d, w, lam), rel=1e-14)
