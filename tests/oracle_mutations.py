@@ -11,7 +11,9 @@ so that the audit's coverage is explicit.
 
 Prints one line per mutation (CAUGHT with the first failing pin, or
 SURVIVED) and exits 1 if a non-equivalent mutation survives.  The copies go
-to DIR (default: a temporary directory); the repository is not modified.
+to DIR (default: the git-ignored .pytest_tmp/oracle_mutations of the
+repository) and are removed as each run ends; the tracked files are not
+modified.
 """
 import argparse
 import concurrent.futures as cf
@@ -19,7 +21,6 @@ import os
 import shutil
 import subprocess
 import sys
-import tempfile
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -235,7 +236,8 @@ def main():
     ap.add_argument("--workdir", default=None)
     ap.add_argument("which", nargs="*", type=int)
     a = ap.parse_args()
-    work = a.workdir or tempfile.mkdtemp(prefix="oracle_mutations_")
+    work = a.workdir or os.path.join(ROOT, ".pytest_tmp", "oracle_mutations")
+    os.makedirs(work, exist_ok=True)
     idx = a.which or list(range(len(MUTATIONS)))
     bad_idx = [i for i in idx if not 0 <= i < len(MUTATIONS)]
     if bad_idx:
@@ -254,8 +256,6 @@ def main():
     caught = sum(res[i].startswith("CAUGHT") for i in idx)
     n_eq = sum(MUTATIONS[i][4] is not None for i in idx)
     print(f"{caught} of {len(idx)} caught; {n_eq} marked equivalent; {bad} non-equivalent not caught")
-    if not a.workdir:
-        shutil.rmtree(work, ignore_errors=True)
     return 1 if bad else 0
 
 
