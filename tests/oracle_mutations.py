@@ -11,9 +11,9 @@ so that the audit's coverage is explicit.
 
 Prints one line per mutation (CAUGHT with the first failing pin, or
 SURVIVED) and exits 1 if a non-equivalent mutation survives.  The copies go
-to DIR (default: the git-ignored .pytest_tmp/oracle_mutations of the
-repository) and are removed as each run ends; the tracked files are not
-modified.
+to DIR (default: the git-ignored .mutation_tmp of the repository, apart
+from pytest's own temporary directory, which pytest empties at every start)
+and are removed as each run ends; the tracked files are not modified.
 """
 import argparse
 import concurrent.futures as cf
@@ -236,7 +236,7 @@ def main():
     ap.add_argument("--workdir", default=None)
     ap.add_argument("which", nargs="*", type=int)
     a = ap.parse_args()
-    work = a.workdir or os.path.join(ROOT, ".pytest_tmp", "oracle_mutations")
+    work = a.workdir or os.path.join(ROOT, ".mutation_tmp")
     os.makedirs(work, exist_ok=True)
     idx = a.which or list(range(len(MUTATIONS)))
     bad_idx = [i for i in idx if not 0 <= i < len(MUTATIONS)]
